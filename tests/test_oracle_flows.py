@@ -1,0 +1,179 @@
+"""Pins of the oracle's whole-case behaviour against closed-form flows and invariants.
+
+Each tolerance comes from the discretisation order of the piece being pinned: viscosity and
+second-order rates (Taylor-Green decay, second-order convergence), body force plus walls
+(pipe start-up series and plane Poiseuille), Bouzidi interpolation (exact-q walls beat the
+staircase, second-order convergence), pulsatile forcing (Womersley), the open boundaries
+(imposed values exact, steady mass flux continuous), and exact mass conservation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_11107_gb300 import inputs as I
+
+from . import analytic
+
+oracle.set_threads(min(8, max(1, oracle.get_threads())))
+
+
+def _tg_rate_error(N, tau=0.8):
+    nu = (tau - 0.5) / 3.0
+    rho, u = I.taylor_green(N, N, 1, 0.01)
+    c = oracle.Case(np.ones((1, N, N), np.uint8), periodic=(1, 1, 1), tau=tau)
+    c.init_equilibrium(rho, u)
+    k2 = 2 * (2 * math.pi / N) ** 2
+    t1, t2 = 50, int(50 + 2 / (nu * k2))
+    c.step(t1)
+    _, u1 = c.macroscopic()
+    c.step(t2 - t1)
+    _, u2 = c.macroscopic()
+    rate = math.log(np.sum(u1[0] * u[0]) / np.sum(u2[0] * u[0])) / (t2 - t1)
+    return abs(rate / (nu * k2) - 1.0)
+
+
+def test_taylor_green_decay_rate_second_order():
+    """Viscosity nu = cs^2 (tau - 1/2) from the second-order rates (Sec. 2.1.3): the vortex
+    decays as exp(-nu k^2 t), with an error that falls 4x per doubling of resolution."""
+    e16 = _tg_rate_error(16)
+    e32 = _tg_rate_error(32)
+    assert e16 < 2.5e-3
+    assert e32 < 6e-4
+    assert e16 / e32 > 3.0
+
+
+def _pipe_slab(bouzidi):
+    g = I.pipe(32, 32, 1, 12.0, center=(16.0, 16.0), tau=0.6, g0=(0.0, 0.0, 1e-6), bouzidi=bouzidi)
+    c = oracle.Case(g.mask, periodic=(0, 0, 1), links=g.links, tau=g.tau, g0=g.g0)
+    c.step(1000)
+    _, u = c.macroscopic()
+    x = np.arange(32) + 0.5
+    X, Y = np.meshgrid(x, x)
+    r = np.hypot(X - 16, Y - 16)
+    fl = g.mask[0] > 0
+    ua = analytic.pipe_startup(r, 1000, 12.0, 1e-6, 0.1 / 3.0)
+    return np.linalg.norm(u[2, 0][fl] - ua[fl]) / np.linalg.norm(ua[fl])
+
+
+def test_pipe_startup_series():
+    """Body-force start-up flow in the radius-12 pipe (tau 0.6, g 1e-6) after 1000 steps vs
+    the Bessel series: within 8% (L2) on the staircase wall, within 2% with exact-q Bouzidi
+    walls, and Bouzidi at least 3x closer."""
+    e_bb = _pipe_slab(False)
+    e_bz = _pipe_slab(True)
+    assert e_bb < 0.08
+    assert e_bz < 0.02
+    assert e_bb > 3 * e_bz
+
+
+def _channel(scale, bouzidi, q_half=False):
+    ny, lo, hi = 20 * scale, 2.3 * scale, 17.2 * scale
+    g = 1e-6 / scale ** 2
+    ch = I.plane_channel(ny, lo, hi, tau=0.8, g=g, bouzidi=bouzidi)
+    links = ch.links
+    if q_half:
+        links = (links[0], links[1], np.full(len(links[0]), 0.5))
+    c = oracle.Case(ch.mask, periodic=ch.periodic, links=links, tau=ch.tau, g0=ch.g0)
+    c.step(5000 * scale * scale)
+    _, u = c.macroscopic()
+    y = np.arange(ny) + 0.5
+    fl = ch.mask[0, :, 0] > 0
+    ua = analytic.plane_poiseuille(y, lo, hi, g, 0.1)
+    return np.abs(u[0, 0, :, 0][fl] - ua[fl]).max() / ua.max(), u
+
+
+def test_bouzidi_channel_second_order():
+    """Sec. 2.1.4: plates at y = 2.3 and 17.2 (q = 0.2 and 0.7, both branches); the steady
+    profile matches the parabola within 1%, converges at second order, and beats halfway
+    bounce-back on the staircase by 5x."""
+    e1, _ = _channel(1, True)
+    e2, _ = _channel(2, True)
+    e_bb, _ = _channel(1, False)
+    assert e1 < 0.01
+    assert e1 / e2 > 3.0
+    assert e_bb > 5 * e1
+
+
+def test_bouzidi_half_is_halfway_bounce_back():
+    """q = 1/2 on every link reproduces halfway bounce-back exactly."""
+    _, u_half = _channel(1, True, q_half=True)
+    _, u_bb = _channel(1, False)
+    assert np.array_equal(u_half, u_bb)
+
+
+def _womersley(bouzidi):
+    R, tau, nu, Wo = 10.0, 0.8, 0.1, 4.0
+    om = Wo ** 2 * nu / R ** 2
+    g = I.pipe(24, 24, 1, R, tau=tau, gamp=(0, 0, 1e-5), gomega=om, bouzidi=bouzidi)
+    c = oracle.Case(g.mask, periodic=g.periodic, links=g.links, tau=tau, gamp=g.gamp, gomega=om)
+    T = 2 * math.pi / om
+    c.step(int(6 * T))
+    x = np.arange(24) + 0.5
+    X, Y = np.meshgrid(x, x)
+    r = np.hypot(X - 12, Y - 12)
+    fl = g.mask[0] > 0
+    err = 0.0
+    for _ in range(8):
+        _, u = c.macroscopic()
+        ua = analytic.womersley(r, c.time, R, 1e-5, om, nu)
+        err = max(err, np.abs(u[2, 0][fl] - ua[fl]).max())
+        c.step(int(T / 8))
+    return err / (1e-5 / om)
+
+
+def test_womersley_pulsatile_pipe():
+    """Sinusoidal body force, Wo = 4: the periodic state matches the complex-Bessel solution
+    within 2.5% of A/omega with exact-q walls, and the staircase is at least 2x worse."""
+    e_bz = _womersley(True)
+    e_bb = _womersley(False)
+    assert e_bz < 0.025
+    assert e_bb > 2 * e_bz
+
+
+def test_open_boundaries_pipe():
+    """Velocity inlet and density outlet (Sec. 2.2): the imposed inlet velocity and outlet
+    density hold exactly and the steady mass flux is the same through every section."""
+    g = I.inlet_pipe(24, 12, 12, 4.5, u_peak=0.01, tau=0.8)
+    c = oracle.Case(g.mask, periodic=g.periodic, inlet_center=g.inlet_center,
+                    inlet_radius=g.inlet_radius, tau=g.tau)
+    a, b, P, up = g.wave
+    c.set_waveform(a, b, P, up)
+    c.step(3000)
+    rho, u = c.macroscopic()
+    inl = g.mask[:, :, 0] == 2
+    y = np.arange(12) + 0.5
+    Y, Z = np.meshgrid(y, y)
+    phi = np.maximum(0.0, 2 * (1 - ((Y - 6) ** 2 + (Z - 6) ** 2) / 4.5 ** 2))
+    assert np.abs(u[0][:, :, 0][inl] - 0.01 * phi[inl]).max() < 1e-15
+    assert np.abs(u[1][:, :, 0][inl]).max() < 1e-15
+    assert np.abs(rho[:, :, -1][g.mask[:, :, -1] == 3] - 1.0).max() < 1e-14
+    flux = (rho * u[0]).sum(axis=(0, 1))
+    assert np.abs(flux / flux.mean() - 1.0).max() < 1e-3
+    # density falls monotonically from inlet to outlet (pressure-driven)
+    assert np.all(np.diff(rho[6, 6, 1:]) < 0)
+
+
+def test_mass_conserved_closed_domain():
+    """Periodic + halfway bounce-back domain: total mass is constant to round-off."""
+    g = I.poiseuille_pipe_32()
+    c = oracle.Case(g.mask[:4].copy(), periodic=g.periodic, tau=g.tau, g0=g.g0)
+    r0, _ = c.macroscopic()
+    c.step(300)
+    r1, _ = c.macroscopic()
+    assert abs(r1.sum() / r0.sum() - 1.0) < 1e-12
+
+
+def test_translational_invariance():
+    """A z-periodic, z-invariant case gives the same fields on a 1-layer and a 4-layer slab,
+    which lets the oracle check full-length pipe runs from a single slab."""
+    g = I.poiseuille_pipe_32()
+    c1 = oracle.Case(g.mask[:1].copy(), periodic=g.periodic, tau=g.tau, g0=g.g0)
+    c4 = oracle.Case(g.mask[:4].copy(), periodic=g.periodic, tau=g.tau, g0=g.g0)
+    c1.step(50)
+    c4.step(50)
+    _, u1 = c1.macroscopic()
+    _, u4 = c4.macroscopic()
+    for z in range(4):
+        assert np.abs(u4[:, z] - u1[:, 0]).max() < 1e-18
