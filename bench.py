@@ -1,0 +1,301 @@
+"""Benchmark of the fused D3Q27 CHM-MRT stream-collide step on GB300.
+
+Workload: pulsatile (Womersley) pipe flow, radius 28 in a 64x64x256 box periodic along z,
+tau 0.55, Womersley number 4, sinusoidal body force of amplitude 1e-5 -- 632,832 fluid cells.
+One benchmark step = one lattice Boltzmann time step over every fluid cell (one launch of the
+fused kernel).  The L2 cache is flushed (a 512 MB write) before every timed step, outside the
+timed region, so every step streams its populations from HBM.
+
+Metric: fluid MLUPS (million fluid-cell updates per second) and the fraction of the measured HBM
+copy bandwidth achieved with the algorithmic 27 reads + 27 writes per update (216 B in FP32,
+108 B in FP16/BF16).
+
+Arms:
+  default            the CUDA library (this repository), FP32 storage as the headline, FP16 and
+                     BF16 storage as variants; plus an end-to-end figure through the public API
+                     with host buffers, and the FP64 oracle timed on the host cores.
+  --impl reference   the FP64 CPU oracle alone on the same workload (bounded sample: the
+                     one-layer z-slab, exact for this z-invariant flow), on the host cores.
+Multi-GPU (torchrun): each rank runs an independent replica of the workload (weak scaling);
+value = total updates of all ranks / max time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "womersley_pipe_64x64x256_R28_Wo4_tau0.55"
+METRIC = "fluid MLUPS, D3Q27 CHM-MRT fused stream-collide (% of measured HBM roofline)"
+BYTES_PER_VALUE = {"fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_oracle_sample(seconds, threads=None):
+    """The FP64 oracle on the workload's one-layer z-slab (2472 fluid cells), advanced in
+    chunks until `seconds` of CPU work have passed; returns (MLUPS, threads, description)."""
+    import oracle
+    from paper_2101_11107_gb300 import inputs as I
+
+    if threads:
+        oracle.set_threads(threads)
+    g = I.womersley_pipe()
+    slab = g.mask[:1].copy()
+    c = oracle.Case(slab, periodic=g.periodic, tau=g.tau, gamp=g.gamp, gomega=g.gomega)
+    c.step(5)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        c.step(20)
+        n += 20
+    dt = time.perf_counter() - t0
+    nf = c.nfluid
+    return nf * n / dt / 1e6, oracle.get_threads(), f"{n} steps of the 64x64x1 z-slab ({nf} fluid cells), {dt:.1f} s"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_steps(dom, steps, warmup, flush, stream):
+    """Per-step CUDA-event times (ms) of `steps` single-step launches, L2 flushed before each."""
+    import torch
+
+    dom.step(warmup)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.add_(1)
+        starts[k].record(stream)
+        dom.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per = max(0.2, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+        for _ in range(args.warmup):
+            run_oracle_sample(per)
+        vals = []
+        desc = ""
+        thr = 1
+        for _ in range(args.steps):
+            v, thr, desc = run_oracle_sample(per)
+            vals.append(v)
+        value = statistics.mean(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1000.0, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "storage": "fp64 (oracle)", "sample": "64x64x1 z-slab"},
+                "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": thr, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+    from paper_2101_11107_gb300 import build as lib_build
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    lib_build.build()
+    from paper_2101_11107_gb300 import inputs as I
+    from paper_2101_11107_gb300 import lbm
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.zeros(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g = I.womersley_pipe()
+    hbm_peak, peak_kind = measured_peaks()
+
+    results = {}
+    clocks = None
+    for storage in (["fp32"] if args.no_variants else ["fp32", "fp16", "bf16"]):
+        dom = lbm.Domain.from_geometry(g, storage=storage)
+        info = dom.info()
+        nf = info["n_fluid"]
+        if storage == "fp32":
+            sampler = ClockSampler(local)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            with sampler:
+                t0 = time.perf_counter()
+                times = time_steps(dom, args.steps, args.warmup, flush, stream)
+                wall = time.perf_counter() - t0
+            clocks = sampler.summary()
+            if world > 1:
+                torch.cuda.synchronize()
+                torch.distributed.barrier()
+        else:
+            times = time_steps(dom, args.steps, args.warmup, flush, stream)
+        ms = statistics.mean(times)
+        bytes_alg = 2 * 27 * BYTES_PER_VALUE[storage] * nf
+        results[storage] = {"ms_per_step": ms, "mlups": nf / (ms * 1e-3) / 1e6, "fluid_cells": nf,
+                            "algorithmic_bytes_per_launch": bytes_alg,
+                            "achieved_gbs": bytes_alg / (ms * 1e-3) / 1e9,
+                            "device_bytes": info["device_bytes"], "slots": info["n_slots"]}
+        if storage != "fp32":
+            dom.close()
+        else:
+            main_dom = dom
+
+    main = results["fp32"]
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * main["fluid_cells"] * args.steps / (total_ms * 1e-3) / 1e6
+
+    # end to end through the public API, host buffers: upload the initial macroscopic state from
+    # pinned host memory, advance 200 steps, read rho and u back to pinned host memory
+    inner = 200
+    nz, ny, nx = g.mask.shape
+    nbox = nx * ny * nz
+    rho_h = torch.ones(nbox, dtype=torch.float32).pin_memory().numpy().reshape(nz, ny, nx)
+    u_h = torch.zeros(3 * nbox, dtype=torch.float32).pin_memory().numpy().reshape(3, nz, ny, nx)
+    rho_o = torch.empty(nbox, dtype=torch.float32).pin_memory().numpy()
+    u_o = torch.empty(3 * nbox, dtype=torch.float32).pin_memory().numpy()
+    L = lbm.load_library()
+    import ctypes
+    e2e_steps = max(3, min(10, args.steps // 20))
+    main_dom.init_equilibrium(rho_h, u_h)
+    main_dom.step(inner)
+    L.lbm_get_macroscopic(main_dom._h, ctypes.c_void_p(rho_o.ctypes.data), ctypes.c_void_p(u_o.ctypes.data), 1, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        main_dom.init_equilibrium(rho_h, u_h)
+        main_dom.step(inner)
+        st = L.lbm_get_macroscopic(main_dom._h, ctypes.c_void_p(rho_o.ctypes.data),
+                                   ctypes.c_void_p(u_o.ctypes.data), 1, 0)
+        assert st == 0
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = world * main["fluid_cells"] * inner / e2e_s / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, thr, desc = run_oracle_sample(args.cpu_seconds)
+        cpu = {"value": v, "unit": "MLUPS", "cores": thr, "kind": "oracle", "sample": desc}
+
+    if rank != 0:
+        return
+    achieved = main["achieved_gbs"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "storage": "fp32 deviations", "fluid_cells": main["fluid_cells"],
+                   "box": [nx, ny, nz], "l2": "flushed before every timed step (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "bytes_per_update_algorithmic": 216, "wall_s_timed_loop": wall},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nbox, "d2h_bytes_per_step": 16 * nbox,
+                "inner_lbm_steps": inner},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "variants": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()}
+                     for k, r in results.items()},
+    }
+    for k, r in results.items():
+        line["variants"][k]["roofline_frac"] = round(r["achieved_gbs"] / hbm_peak, 4)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

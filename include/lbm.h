@@ -1,0 +1,188 @@
+/*
+ * lbm.h -- C-ABI of the GB300 D3Q27 central-Hermite-moment MRT lattice Boltzmann library.
+ *
+ * The library advances the lattice Boltzmann equation (Hosseini et al., Sec. 2.1.1) with the
+ * CHM-MRT collision operator Omega = T^-1 S T (f_eq - f) and the fully expanded equilibrium
+ * (Sec. 2.1.3), halfway bounce-back walls, Bouzidi interpolated walls (Sec. 2.1.4) and a
+ * pulsatile velocity inlet / density outlet (Sec. 2.2), on a voxelised geometry, as
+ * hand-written CUDA kernels on one GPU.
+ *
+ * Conventions used by every entry point:
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3.  Directions i = (cx+1) + 3 (cy+1) + 9 (cz+1),
+ *     c in {-1,0,1}^3; the opposite of i is 26 - i.
+ *   - Box arrays are dense, x fastest: index = x + nx (y + ny z).  Cell (x,y,z) has its centre
+ *     at (x + 1/2, y + 1/2, z + 1/2).
+ *   - Time level n: the populations f(x, n) after streaming, wall rules and open-boundary
+ *     closures.  lbm_step(dom, k) advances n -> n + k; one step collides with the body force
+ *     g(n), streams, and closes the open boundaries with the inflow U(n + 1).  A new domain is
+ *     at n = 0 with f = w (rho = 1, u = 0) closed at n = 0.
+ *   - Velocities reported at level n are u = (sum_i c_i f_i)/rho + g(n)/2 (half-force shift).
+ *   - Ownership: the caller owns every pointer it passes; the library copies what it keeps
+ *     during the call.  The library owns the device memory of a domain, obtained through the
+ *     allocator callbacks given at creation (cudaMalloc/cudaFree when they are NULL), and
+ *     releases it in lbm_destroy.
+ *   - Errors: every call returns an lbm_status; no C++ exception crosses this boundary.  On
+ *     failure lbm_last_error() returns a message for the calling thread.  Calls that only
+ *     enqueue work report launch errors; faults inside a kernel surface at the next call that
+ *     synchronises (lbm_get_macroscopic, lbm_get_diagnostics, lbm_sync, lbm_save_state).
+ *   - Streams: all device work of a domain is enqueued on the CUDA stream given at creation
+ *     (NULL = the legacy default stream).  Calls on one domain must not run concurrently from
+ *     several host threads.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain lbm_domain;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* bad argument; nothing was changed */
+    LBM_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    LBM_ERR_OOM = 3,         /* the allocator returned NULL */
+    LBM_ERR_UNSTABLE = 4,    /* a NaN/Inf was found in the populations */
+    LBM_ERR_TIMEOUT = 5,     /* a device-side wait gave up (bounded spin) */
+    LBM_ERR_STATE = 6,       /* call not valid in the domain's current state */
+    LBM_ERR_IO = 7           /* file could not be read or written, or does not match */
+} lbm_status;
+
+/* Storage of the populations in HBM.  All arithmetic is FP32 in every mode.
+ *   FP32: the deviation f_i - w_i, FP32.
+ *   FP16 / BF16: the scaled deviation (f_i - w_i) / w_i in 16 bits. */
+typedef enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1, LBM_STORE_BF16 = 2 } lbm_storage;
+
+/* Physical parameters (Sec. 2.1.3: S is diagonal in central Hermite moment space). */
+typedef struct {
+    double tau;          /* relaxation time of the six second-order moments: rate 1/tau,
+                            kinematic viscosity nu = (tau - 1/2)/3; must be > 1/2 */
+    double omega_hi[4];  /* rates of the 3rd, 4th, 5th and 6th-order moments (free parameters
+                            of the paper), each in (0, 2); default 1 */
+    double force[3];     /* constant body acceleration g0 (force density rho g) */
+    double force_amp[3]; /* g(n) = force + force_amp cos(force_omega n) */
+    double force_omega;  /* angular frequency per step of the body-force modulation */
+    double rho_out;      /* density imposed at outlet cells; default 1 */
+    int32_t periodic[3]; /* nonzero: the axis wraps (its extent must be a multiple of 4) */
+    int32_t storage;     /* lbm_storage */
+} lbm_params;
+
+/* Device memory callbacks: return a device pointer aligned to 256 bytes, or NULL. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*lbm_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+    int32_t nx, ny, nz;
+    int64_t n_fluid;         /* cells updated per step (mask 1, 2 or 3) */
+    int64_t n_bricks;        /* 4x4x4 bricks holding at least one fluid cell */
+    int64_t n_slots;         /* 64 * n_bricks: population slots per direction */
+    int64_t n_wall_cells;    /* fluid cells with at least one wall link */
+    int64_t n_bouzidi_cells; /* fluid cells with at least one Bouzidi link */
+    int64_t n_open_cells;    /* inlet + outlet cells */
+    int64_t time;            /* current time level n */
+    int32_t storage;
+    int32_t bytes_per_value; /* 4 (FP32) or 2 (FP16/BF16) */
+    int64_t device_bytes;    /* device memory held by the domain */
+} lbm_info;
+
+typedef struct {
+    double mass;     /* sum of rho over fluid cells (FP64 accumulation) */
+    double flux_in;  /* sum over inlet cells of rho u . n_in (n_in the inward normal) */
+    double flux_out; /* sum over outlet cells of -rho u . n_in (outflow positive) */
+    double max_u;    /* max |u| over fluid cells */
+    int64_t n_nonfinite; /* fluid cells whose rho or u is NaN or Inf */
+    int64_t time;
+} lbm_diagnostics;
+
+/* Fills *p with the defaults: tau 0.6, omega_hi 1, no force, rho_out 1, not periodic, FP32. */
+void lbm_default_params(lbm_params* p);
+
+/*
+ * Builds a domain from a voxel mask (Sec. 2.2: voxelised vessel geometry).
+ *   mask[nx*ny*nz]: 0 solid, 1 fluid, 2 velocity inlet, 3 density outlet.  Inlet and outlet
+ *     cells must lie on exactly one non-periodic box face; the face's inward normal is theirs.
+ *     Neighbours outside a non-periodic face count as solid.
+ *   Wall links (Sec. 2.1.4, q = |x_f - x_s| / |c|), n_links entries, may be 0 / NULL:
+ *     link_cell[l]  box index of a cell with mask 1,
+ *     link_dir[l]   direction beta with x_f + c_beta not fluid,
+ *     link_q[l]     q in (0, 1]: the wall cuts the segment x_f -> x_f + c_beta at q.
+ *     Wall links without an entry use halfway bounce-back.  Duplicates are rejected.
+ *   inlet_center[3], inlet_radius: the inflow profile u = U(n) 2 (1 - r^2/R^2) n_in, r the
+ *     distance from the cell centre to inlet_center in the inlet plane (0 beyond R).  May be
+ *     NULL / ignored when the mask has no inlet cells.
+ *   params: see lbm_params; NULL means lbm_default_params.
+ *   alloc/release/alloc_ctx: device allocator (both NULL: cudaMalloc / cudaFree).
+ *   cuda_stream: cudaStream_t for all work of the domain (NULL: legacy default stream).
+ *   *out receives the domain, or NULL on failure.
+ * Errors: INVALID_ARG (sizes, mask values, links, parameters), OOM, CUDA.
+ */
+lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz,
+                             const int64_t* link_cell, const uint8_t* link_dir,
+                             const double* link_q, int64_t n_links, const double* inlet_center,
+                             double inlet_radius, const lbm_params* params, lbm_alloc_fn alloc,
+                             lbm_free_fn release, void* alloc_ctx, void* cuda_stream,
+                             lbm_domain** out);
+
+/*
+ * Sets the inflow waveform (Sec. 2.2: inflow curve over one cycle):
+ *   s(t) = a[0] + sum_{k=1..n_harm} a[k] cos(2 pi k t / P) + b[k-1] sin(2 pi k t / P),
+ *   U(t) = u_peak s(t) / max_{t = 0..P-1} s(t),   P = period_steps (an integer >= 1).
+ * The domain's inlet cells are re-closed at the current level.  Until this is called U = 0.
+ * Errors: INVALID_ARG (n_harm outside 0..15, P not a positive integer <= 2^24, max s <= 0).
+ */
+lbm_status lbm_set_inlet_waveform(lbm_domain* dom, const double* a, const double* b,
+                                  int32_t n_harm, double period_steps, double u_peak);
+
+/*
+ * Initial condition from macroscopic fields (dense box arrays; rho[nx*ny*nz], u = three planes
+ * ux, uy, uz of nx*ny*nz each): the post-collision populations of level n - 1 are set to
+ * f_eq(rho, u) (full expansion) at every fluid cell, so that level n is their stream with the
+ * wall rules and closures.  device_ptrs != 0: rho and u are device pointers.
+ */
+lbm_status lbm_init_equilibrium(lbm_domain* dom, const float* rho, const float* u,
+                                int32_t device_ptrs);
+
+/* Enqueues n >= 0 fused stream-collide steps (Sec. 2.1.1, 2.1.3, 2.1.4) on the domain's
+ * stream; returns without waiting.  Errors: INVALID_ARG (n < 0), CUDA (launch failure). */
+lbm_status lbm_step(lbm_domain* dom, int64_t n);
+
+/*
+ * rho and u = (sum c f)/rho + g(n)/2 at the current level n (Sec. 2.1.1 moments).
+ *   dense != 0: rho[nx*ny*nz] and u[3][nx*ny*nz] on the box, solid cells 0.
+ *   dense == 0: rho[n_fluid], u[3][n_fluid], fluid cells in increasing box index.
+ *   device_ptrs != 0: rho and u are device pointers (written on the domain's stream);
+ *   otherwise host pointers (the call stages through device memory and waits).
+ */
+lbm_status lbm_get_macroscopic(lbm_domain* dom, float* rho, float* u, int32_t dense,
+                               int32_t device_ptrs);
+
+/* FP64 reductions over the current level (mass, inlet/outlet flux, max |u|, non-finite
+ * count); waits for the stream.  Returns UNSTABLE (after filling *out) if any fluid cell is
+ * non-finite.  The reduction order is fixed, so results are reproducible run to run. */
+lbm_status lbm_get_diagnostics(lbm_domain* dom, lbm_diagnostics* out);
+
+lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
+
+/* Waits for all work enqueued on the domain. */
+lbm_status lbm_sync(lbm_domain* dom);
+
+/* Checkpoint: the stored populations (in storage precision), the time level, the waveform and
+ * the parameters, to a binary file.  lbm_load_state restores them into a domain built from the
+ * same mask and links (IO on a mismatch).  Both wait for the stream. */
+lbm_status lbm_save_state(lbm_domain* dom, const char* path);
+lbm_status lbm_load_state(lbm_domain* dom, const char* path);
+
+/* Releases the domain and its device memory (after waiting for its stream). NULL is a no-op. */
+void lbm_destroy(lbm_domain* dom);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -1,0 +1,702 @@
+// lbm_domain.cu -- host side of the C-ABI (include/lbm.h): validation, the brick layout of a
+// voxel domain, device memory through the caller's allocator, time levels, checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lbm_status fail(lbm_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct lbm_domain {
+    int32_t nx = 0, ny = 0, nz = 0;
+    lbm_params params{};
+    int64_t n_fluid = 0, n_bricks = 0, n_slots = 0, n_bq = 0, n_io = 0, n_wall = 0;
+    DomainView view{};
+    int32_t* d_fl_slot = nullptr;
+    int32_t* d_fl_box = nullptr;
+    void* d_pop[2] = {nullptr, nullptr};
+    int cur = 0;  // d_pop[cur] holds the post-collision populations of level time - 1
+    double* d_partials = nullptr;
+    lbm_diagnostics* d_diag = nullptr;
+    int64_t time = 0;
+    // inflow waveform, tabulated over one period in FP64 and rounded to FP32
+    bool has_wave = false;
+    std::vector<float> wave;
+    std::vector<double> wave_a, wave_b;
+    double wave_period = 0.0, wave_peak = 0.0;
+    cudaStream_t stream = nullptr;
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn release = nullptr;
+    void* alloc_ctx = nullptr;
+    std::vector<void*> owned;
+    int64_t device_bytes = 0;
+    // host copies kept for checkpoints
+    uint64_t geometry_hash = 0;
+
+    int bytes_per_value() const { return params.storage == LBM_STORE_FP32 ? 4 : 2; }
+    size_t pop_bytes() const { return (size_t)Q * (size_t)n_slots * (size_t)bytes_per_value(); }
+
+    void* dev_alloc(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        void* p = nullptr;
+        if (alloc) {
+            p = alloc(bytes, alloc_ctx);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) {
+            owned.push_back(p);
+            device_bytes += (int64_t)bytes;
+        }
+        return p;
+    }
+
+    // gives back one buffer obtained from dev_alloc
+    void dev_free(void* p, size_t bytes)
+    {
+        auto it = std::find(owned.begin(), owned.end(), p);
+        if (it == owned.end()) return;
+        owned.erase(it);
+        device_bytes -= (int64_t)(((bytes + 255) & ~(size_t)255) ? ((bytes + 255) & ~(size_t)255) : 256);
+        if (release) release(p, alloc_ctx);
+        else if (!alloc) cudaFree(p);
+    }
+
+    void release_all()
+    {
+        for (void* p : owned) {
+            if (release) release(p, alloc_ctx);
+            else if (!alloc) cudaFree(p);
+        }
+        owned.clear();
+    }
+
+    LevelArgs level_args(int64_t n) const
+    {
+        LevelArgs a{};
+        for (int d = 0; d < 3; ++d)
+            a.g[d] = (float)(params.force[d] + params.force_amp[d] * std::cos(params.force_omega * (double)n));
+        a.U = 0.0f;
+        if (has_wave && !wave.empty()) a.U = wave[(size_t)(n % (int64_t)wave.size())];
+        a.s2 = (float)(1.0 / params.tau);
+        a.s3 = (float)params.omega_hi[0];
+        a.s4 = (float)params.omega_hi[1];
+        a.s5 = (float)params.omega_hi[2];
+        a.s6 = (float)params.omega_hi[3];
+        a.rho_out = (float)params.rho_out;
+        return a;
+    }
+};
+
+namespace {
+
+template <class T>
+lbm_status upload(lbm_domain* D, T** dst, const std::vector<T>& src, const char* what)
+{
+    *dst = static_cast<T*>(D->dev_alloc(sizeof(T) * std::max<size_t>(src.size(), 1)));
+    if (!*dst) return fail(LBM_ERR_OOM, std::string("allocation failed: ") + what);
+    if (!src.empty()) {
+        cudaError_t e = cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, D->stream);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+    return LBM_OK;
+}
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n)
+{
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+lbm_status check_params(const lbm_params& p)
+{
+    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return fail(LBM_ERR_INVALID_ARG, "tau must be > 1/2");
+    for (int k = 0; k < 4; ++k)
+        if (!(p.omega_hi[k] > 0.0 && p.omega_hi[k] < 2.0))
+            return fail(LBM_ERR_INVALID_ARG, "omega_hi must lie in (0, 2)");
+    if (!(p.rho_out > 0.0) || !std::isfinite(p.rho_out)) return fail(LBM_ERR_INVALID_ARG, "rho_out must be > 0");
+    if (p.storage < LBM_STORE_FP32 || p.storage > LBM_STORE_BF16) return fail(LBM_ERR_INVALID_ARG, "bad storage");
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p.force[d]) || !std::isfinite(p.force_amp[d]))
+            return fail(LBM_ERR_INVALID_ARG, "non-finite force");
+    if (!std::isfinite(p.force_omega)) return fail(LBM_ERR_INVALID_ARG, "non-finite force_omega");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->tau = 0.6;
+    for (int k = 0; k < 4; ++k) p->omega_hi[k] = 1.0;
+    p->rho_out = 1.0;
+    p->storage = LBM_STORE_FP32;
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz, const int64_t* link_cell,
+                             const uint8_t* link_dir, const double* link_q, int64_t n_links,
+                             const double* inlet_center, double inlet_radius, const lbm_params* params,
+                             lbm_alloc_fn alloc, lbm_free_fn release, void* alloc_ctx, void* cuda_stream,
+                             lbm_domain** out)
+{
+    g_last_error.clear();
+    if (!out) return fail(LBM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!mask) return fail(LBM_ERR_INVALID_ARG, "mask is NULL");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(LBM_ERR_INVALID_ARG, "box extents must be positive");
+    const int64_t n_box = (int64_t)nx * ny * nz;
+    if (n_box >= ((int64_t)1 << 31)) return fail(LBM_ERR_INVALID_ARG, "box has 2^31 cells or more");
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(LBM_ERR_INVALID_ARG, "give both allocator callbacks or neither");
+    if (n_links < 0 || (n_links > 0 && (!link_cell || !link_dir || !link_q)))
+        return fail(LBM_ERR_INVALID_ARG, "bad link arrays");
+    lbm_params P;
+    if (params) P = *params;
+    else lbm_default_params(&P);
+    if (lbm_status s = check_params(P)) return s;
+    const int n3[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        P.periodic[d] = P.periodic[d] ? 1 : 0;
+        if (P.periodic[d] && n3[d] % BRICK_EDGE != 0)
+            return fail(LBM_ERR_INVALID_ARG, "a periodic axis must have an extent that is a multiple of 4");
+    }
+
+    // ---------------------------------------------------------------- bricks
+    const int nbx = (nx + 3) / 4, nby = (ny + 3) / 4, nbz = (nz + 3) / 4;
+    const int64_t n_brick_box = (int64_t)nbx * nby * nbz;
+    std::vector<int32_t> brick_id((size_t)n_brick_box, -1);
+    int64_t n_fluid = 0;
+    for (int64_t b = 0; b < n_box; ++b) {
+        if (mask[b] > 3) return fail(LBM_ERR_INVALID_ARG, "mask value > 3");
+        if (mask[b]) ++n_fluid;
+    }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                if (mask[x + (int64_t)nx * (y + (int64_t)ny * z)])
+                    brick_id[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nby * (z >> 2))] = 0;
+    int64_t n_bricks = 0;
+    std::vector<int32_t> brick_pos;  // (bx, by, bz) per brick
+    for (int64_t bb = 0; bb < n_brick_box; ++bb)
+        if (brick_id[bb] == 0) {
+            brick_id[bb] = (int32_t)n_bricks++;
+            brick_pos.push_back((int32_t)(bb % nbx));
+            brick_pos.push_back((int32_t)((bb / nbx) % nby));
+            brick_pos.push_back((int32_t)(bb / ((int64_t)nbx * nby)));
+        }
+    const int64_t n_slots = n_bricks * BRICK_CELLS;
+    if (n_slots * Q >= ((int64_t)1 << 40)) return fail(LBM_ERR_INVALID_ARG, "domain too large");
+    const int nb3[3] = {nbx, nby, nbz};
+    std::vector<int32_t> nbr((size_t)n_bricks * Q, -1);
+    for (int64_t b = 0; b < n_bricks; ++b) {
+        for (int o = 0; o < Q; ++o) {
+            int p[3] = {brick_pos[3 * b] + cx_of(o), brick_pos[3 * b + 1] + cy_of(o), brick_pos[3 * b + 2] + cz_of(o)};
+            bool ok = true;
+            for (int d = 0; d < 3; ++d) {
+                if (p[d] < 0 || p[d] >= nb3[d]) {
+                    if (P.periodic[d]) p[d] = (p[d] + nb3[d]) % nb3[d];
+                    else ok = false;
+                }
+            }
+            if (ok) nbr[(size_t)b * Q + o] = brick_id[p[0] + (int64_t)nbx * (p[1] + (int64_t)nby * p[2])];
+        }
+    }
+    auto slot_of = [&](int x, int y, int z) -> int64_t {
+        const int64_t b = brick_id[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nby * (z >> 2))];
+        return b * BRICK_CELLS + (x & 3) + ((y & 3) << 2) + ((z & 3) << 4);
+    };
+    // fluid index of the box cell shifted by s * c_i, or -1 (solid / outside a non-periodic face)
+    auto shifted_fluid = [&](int x, int y, int z, int i, int s) -> int64_t {
+        int p[3] = {x + s * cx_of(i), y + s * cy_of(i), z + s * cz_of(i)};
+        for (int d = 0; d < 3; ++d) {
+            if (p[d] < 0 || p[d] >= n3[d]) {
+                if (!P.periodic[d]) return -1;
+                p[d] = (p[d] + n3[d]) % n3[d];
+            }
+        }
+        const int64_t bi = p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2]);
+        return mask[bi] ? bi : -1;
+    };
+
+    // ---------------------------------------------------------------- cell words
+    std::vector<uint32_t> word((size_t)n_slots, 0u);
+    std::vector<int32_t> aux((size_t)n_slots, -1);
+    std::vector<int32_t> fl_slot, fl_box;
+    fl_slot.reserve((size_t)n_fluid);
+    fl_box.reserve((size_t)n_fluid);
+    int64_t n_wall = 0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int64_t bi = x + (int64_t)nx * (y + (int64_t)ny * z);
+                if (!mask[bi]) continue;
+                uint32_t w = WORD_FLUID;
+                for (int i = 0; i < Q; ++i)
+                    if (i != 13 && shifted_fluid(x, y, z, i, -1) < 0) w |= 1u << i;
+                if (w & WORD_WALL_MASK) ++n_wall;
+                const int64_t s = slot_of(x, y, z);
+                word[(size_t)s] = w;
+                fl_slot.push_back((int32_t)s);
+                fl_box.push_back((int32_t)bi);
+            }
+
+    // ---------------------------------------------------------------- open boundaries
+    std::vector<float> io_phi;
+    std::vector<int8_t> io_axis, io_sign;
+    std::vector<std::pair<int64_t, int64_t>> io_cells;  // (slot, box index), sorted by slot
+    for (int64_t k = 0; k < n_fluid; ++k)
+        if (mask[fl_box[(size_t)k]] >= 2) io_cells.push_back({fl_slot[(size_t)k], fl_box[(size_t)k]});
+    std::sort(io_cells.begin(), io_cells.end());
+    for (const auto& c : io_cells) {
+        const int64_t bi = c.second;
+        const int p[3] = {(int)(bi % nx), (int)((bi / nx) % ny), (int)(bi / ((int64_t)nx * ny))};
+        int faces = 0, ax = -1, sg = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (P.periodic[d]) continue;
+            if (p[d] == 0) { ++faces; ax = d; sg = +1; }
+            if (p[d] == n3[d] - 1) { ++faces; ax = d; sg = -1; }
+        }
+        if (faces != 1) return fail(LBM_ERR_INVALID_ARG, "inlet/outlet cell not on exactly one non-periodic face");
+        float phi = 0.0f;
+        if (mask[bi] == 2) {
+            if (!inlet_center || !(inlet_radius > 0.0))
+                return fail(LBM_ERR_INVALID_ARG, "inlet cells need inlet_center and inlet_radius > 0");
+            double r2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                if (d == ax) continue;
+                const double dx = p[d] + 0.5 - inlet_center[d];
+                r2 += dx * dx;
+            }
+            const double v = 2.0 * (1.0 - r2 / (inlet_radius * inlet_radius));
+            phi = (float)(v > 0.0 ? v : 0.0);
+        }
+        const int32_t rec = (int32_t)io_phi.size();
+        io_phi.push_back(phi);
+        io_axis.push_back((int8_t)ax);
+        io_sign.push_back((int8_t)sg);
+        word[(size_t)c.first] |= (uint32_t)(mask[bi] == 2 ? KIND_INLET : KIND_OUTLET) << WORD_KIND_SHIFT;
+        aux[(size_t)c.first] = rec;
+    }
+
+    // ---------------------------------------------------------------- Bouzidi links
+    std::vector<std::pair<int64_t, std::pair<int, float>>> lk;  // (slot, (alpha, q))
+    lk.reserve((size_t)n_links);
+    for (int64_t l = 0; l < n_links; ++l) {
+        const int64_t bi = link_cell[l];
+        const int beta = link_dir[l];
+        const double q = link_q[l];
+        if (bi < 0 || bi >= n_box || beta >= Q || beta == 13 || !(q > 0.0 && q <= 1.0))
+            return fail(LBM_ERR_INVALID_ARG, "link " + std::to_string(l) + " out of range");
+        if (mask[bi] != 1) return fail(LBM_ERR_INVALID_ARG, "link " + std::to_string(l) + ": cell is not a plain fluid cell");
+        const int x = (int)(bi % nx), y = (int)((bi / nx) % ny), z = (int)(bi / ((int64_t)nx * ny));
+        if (shifted_fluid(x, y, z, beta, +1) >= 0)
+            return fail(LBM_ERR_INVALID_ARG, "link " + std::to_string(l) + " does not point into a wall");
+        lk.push_back({slot_of(x, y, z), {Q - 1 - beta, (float)q}});
+    }
+    std::sort(lk.begin(), lk.end(), [](const auto& a, const auto& b) {
+        return a.first != b.first ? a.first < b.first : a.second.first < b.second.first;
+    });
+    int64_t n_bq = 0;
+    for (size_t l = 0; l < lk.size(); ++l) {
+        if (l > 0 && lk[l].first == lk[l - 1].first && lk[l].second.first == lk[l - 1].second.first)
+            return fail(LBM_ERR_INVALID_ARG, "duplicate link");
+        if (l == 0 || lk[l].first != lk[l - 1].first) ++n_bq;
+    }
+    std::vector<float> bq((size_t)Q * (size_t)std::max<int64_t>(n_bq, 1), 0.0f);
+    {
+        int64_t rec = -1;
+        for (size_t l = 0; l < lk.size(); ++l) {
+            if (l == 0 || lk[l].first != lk[l - 1].first) {
+                ++rec;
+                word[(size_t)lk[l].first] |= (uint32_t)KIND_BOUZIDI << WORD_KIND_SHIFT;
+                aux[(size_t)lk[l].first] = (int32_t)rec;
+            }
+            bq[(size_t)lk[l].second.first * (size_t)n_bq + (size_t)rec] = lk[l].second.second;
+        }
+    }
+
+    // ---------------------------------------------------------------- device
+    lbm_domain* D = new (std::nothrow) lbm_domain();
+    if (!D) return fail(LBM_ERR_OOM, "host allocation failed");
+    D->nx = nx;
+    D->ny = ny;
+    D->nz = nz;
+    D->params = P;
+    D->n_fluid = n_fluid;
+    D->n_bricks = n_bricks;
+    D->n_slots = n_slots;
+    D->n_bq = n_bq;
+    D->n_io = (int64_t)io_phi.size();
+    D->n_wall = n_wall;
+    D->stream = static_cast<cudaStream_t>(cuda_stream);
+    D->alloc = alloc;
+    D->release = release;
+    D->alloc_ctx = alloc_ctx;
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, mask, (size_t)n_box);
+    h = fnv1a(h, word.data(), word.size() * sizeof(uint32_t));
+    h = fnv1a(h, bq.data(), bq.size() * sizeof(float));
+    D->geometry_hash = h;
+
+    lbm_status st = LBM_OK;
+    int32_t* d_nbr = nullptr;
+    uint32_t* d_word = nullptr;
+    int32_t* d_aux = nullptr;
+    float* d_bq = nullptr;
+    float* d_io_phi = nullptr;
+    int8_t* d_io_axis = nullptr;
+    int8_t* d_io_sign = nullptr;
+    if (!st) st = upload(D, &d_nbr, nbr, "brick neighbours");
+    if (!st) st = upload(D, &d_word, word, "cell words");
+    if (!st) st = upload(D, &d_aux, aux, "aux index");
+    if (!st) st = upload(D, &d_bq, bq, "Bouzidi q");
+    if (!st) st = upload(D, &d_io_phi, io_phi, "inlet profile");
+    if (!st) st = upload(D, &d_io_axis, io_axis, "open-boundary axis");
+    if (!st) st = upload(D, &d_io_sign, io_sign, "open-boundary sign");
+    if (!st) st = upload(D, &D->d_fl_slot, fl_slot, "fluid slots");
+    if (!st) st = upload(D, &D->d_fl_box, fl_box, "fluid box indices");
+    for (int k = 0; k < 2 && !st; ++k) {
+        D->d_pop[k] = D->dev_alloc(D->pop_bytes());
+        if (!D->d_pop[k]) st = fail(LBM_ERR_OOM, "allocation failed: populations");
+        else {
+            cudaError_t e = cudaMemsetAsync(D->d_pop[k], 0, D->pop_bytes(), D->stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "clearing populations");
+        }
+    }
+    if (!st) {
+        D->d_partials = static_cast<double*>(D->dev_alloc(sizeof(double) * 5 * (size_t)diagnostics_blocks(n_fluid)));
+        D->d_diag = static_cast<lbm_diagnostics*>(D->dev_alloc(sizeof(lbm_diagnostics)));
+        if (!D->d_partials || !D->d_diag) st = fail(LBM_ERR_OOM, "allocation failed: diagnostics");
+    }
+    if (!st) {
+        cudaError_t e = cudaStreamSynchronize(D->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "uploading the domain");
+    }
+    if (st) {
+        cudaStreamSynchronize(D->stream);
+        D->release_all();
+        delete D;
+        return st;
+    }
+    DomainView& v = D->view;
+    v.n_slots = n_slots;
+    v.n_bricks = n_bricks;
+    v.nbr = d_nbr;
+    v.word = d_word;
+    v.aux = d_aux;
+    v.bq = d_bq;
+    v.n_bq = std::max<int64_t>(n_bq, 1);
+    v.io_phi = d_io_phi;
+    v.io_axis = d_io_axis;
+    v.io_sign = d_io_sign;
+    v.n_io = D->n_io;
+    D->cur = 0;
+    D->time = 0;
+    *out = D;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_inlet_waveform(lbm_domain* D, const double* a, const double* b, int32_t n_harm,
+                                  double period_steps, double u_peak)
+{
+    g_last_error.clear();
+    if (!D || !a || (n_harm > 0 && !b)) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    if (n_harm < 0 || n_harm > 15) return fail(LBM_ERR_INVALID_ARG, "n_harm must be in 0..15");
+    if (!(period_steps >= 1.0) || period_steps > 16777216.0 || period_steps != std::floor(period_steps))
+        return fail(LBM_ERR_INVALID_ARG, "period_steps must be a positive integer <= 2^24");
+    if (!std::isfinite(u_peak)) return fail(LBM_ERR_INVALID_ARG, "u_peak must be finite");
+    const int64_t P = (int64_t)period_steps;
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<double> s((size_t)P);
+    double smax = -INFINITY;
+    for (int64_t t = 0; t < P; ++t) {
+        double v = a[0];
+        for (int k = 1; k <= n_harm; ++k) {
+            const double ph = two_pi * k * (double)t / period_steps;
+            v += a[k] * std::cos(ph) + b[k - 1] * std::sin(ph);
+        }
+        s[(size_t)t] = v;
+        smax = std::max(smax, v);
+    }
+    if (!(smax > 0.0)) return fail(LBM_ERR_INVALID_ARG, "the waveform's maximum must be positive");
+    D->wave.resize((size_t)P);
+    for (int64_t t = 0; t < P; ++t) D->wave[(size_t)t] = (float)(u_peak * s[(size_t)t] / smax);
+    D->wave_a.assign(a, a + n_harm + 1);
+    D->wave_b.assign(b ? b : a, b ? b + n_harm : a);
+    D->wave_period = period_steps;
+    D->wave_peak = u_peak;
+    D->has_wave = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_domain* D, const float* rho, const float* u, int32_t device_ptrs)
+{
+    g_last_error.clear();
+    if (!D || !rho || !u) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
+    const float* dr = rho;
+    const float* du = u;
+    float* stage = nullptr;
+    if (!device_ptrs) {
+        stage = static_cast<float*>(D->dev_alloc(sizeof(float) * 4 * (size_t)n_box));
+        if (!stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+        cudaError_t e = cudaMemcpyAsync(stage, rho, sizeof(float) * n_box, cudaMemcpyHostToDevice, D->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(stage + n_box, u, sizeof(float) * 3 * n_box, cudaMemcpyHostToDevice, D->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "uploading fields");
+        dr = stage;
+        du = stage + n_box;
+    }
+    cudaError_t e = launch_init_equilibrium(D->params.storage, D->n_slots, D->d_pop[D->cur], D->d_fl_slot,
+                                            D->d_fl_box, D->n_fluid, dr, du, n_box, D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    if (stage) {
+        e = cudaStreamSynchronize(D->stream);
+        D->dev_free(stage, sizeof(float) * 4 * (size_t)n_box);
+        if (e != cudaSuccess) return cuda_fail(e, "init");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_domain* D, int64_t n)
+{
+    g_last_error.clear();
+    if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
+    if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
+    for (int64_t k = 0; k < n; ++k) {
+        const LevelArgs a = D->level_args(D->time);
+        cudaError_t e = launch_step(D->params.storage, D->view, D->d_pop[D->cur], D->d_pop[1 - D->cur], a, D->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+        D->cur = 1 - D->cur;
+        D->time += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_macroscopic(lbm_domain* D, float* rho, float* u, int32_t dense, int32_t device_ptrs)
+{
+    g_last_error.clear();
+    if (!D || !rho || !u) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n_out = dense ? (int64_t)D->nx * D->ny * D->nz : D->n_fluid;
+    const LevelArgs a = D->level_args(D->time);
+    float* dr = rho;
+    float* du = u;
+    float* stage = nullptr;
+    const size_t bytes = sizeof(float) * 4 * (size_t)std::max<int64_t>(n_out, 1);
+    if (!device_ptrs) {
+        stage = static_cast<float*>(D->dev_alloc(bytes));
+        if (!stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+        dr = stage;
+        du = stage + n_out;
+    }
+    cudaError_t e = cudaSuccess;
+    if (dense) e = cudaMemsetAsync(dr, 0, sizeof(float) * n_out, D->stream);
+    if (dense && e == cudaSuccess) e = cudaMemsetAsync(du, 0, sizeof(float) * 3 * n_out, D->stream);
+    if (e == cudaSuccess)
+        e = launch_macroscopic(D->params.storage, D->view, D->d_pop[D->cur], a, D->d_fl_slot, D->d_fl_box, D->n_fluid,
+                               dense, dr, du, n_out, D->stream);
+    if (stage) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, sizeof(float) * n_out, cudaMemcpyDeviceToHost, D->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, sizeof(float) * 3 * n_out, cudaMemcpyDeviceToHost, D->stream);
+        cudaError_t e2 = cudaStreamSynchronize(D->stream);
+        if (e == cudaSuccess) e = e2;
+        D->dev_free(stage, bytes);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "macroscopic export");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_diagnostics(lbm_domain* D, lbm_diagnostics* out)
+{
+    g_last_error.clear();
+    if (!D || !out) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    const LevelArgs a = D->level_args(D->time);
+    cudaError_t e = launch_diagnostics(D->params.storage, D->view, D->d_pop[D->cur], a, D->d_fl_slot, D->n_fluid,
+                                       D->d_partials, D->d_diag, D->stream);
+    lbm_diagnostics h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, D->d_diag, sizeof(h), cudaMemcpyDeviceToHost, D->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+    h.time = D->time;
+    *out = h;
+    if (h.n_nonfinite > 0) return fail(LBM_ERR_UNSTABLE, "non-finite populations in " + std::to_string(h.n_nonfinite) + " cells");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(const lbm_domain* D, lbm_info* out)
+{
+    g_last_error.clear();
+    if (!D || !out) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    lbm_info I{};
+    I.nx = D->nx;
+    I.ny = D->ny;
+    I.nz = D->nz;
+    I.n_fluid = D->n_fluid;
+    I.n_bricks = D->n_bricks;
+    I.n_slots = D->n_slots;
+    I.n_wall_cells = D->n_wall;
+    I.n_bouzidi_cells = D->n_bq;
+    I.n_open_cells = D->n_io;
+    I.time = D->time;
+    I.storage = D->params.storage;
+    I.bytes_per_value = D->bytes_per_value();
+    I.device_bytes = D->device_bytes;
+    *out = I;
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_domain* D)
+{
+    g_last_error.clear();
+    if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
+    cudaError_t e = cudaStreamSynchronize(D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------------------ checkpoints
+namespace {
+struct CheckpointHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t nx, ny, nz, storage;
+    int64_t n_slots, time;
+    uint64_t geometry_hash;
+    lbm_params params;
+    int32_t has_wave, n_harm;
+    double wave_period, wave_peak;
+};
+const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+}  // namespace
+
+lbm_status lbm_save_state(lbm_domain* D, const char* path)
+{
+    g_last_error.clear();
+    if (!D || !path) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    std::vector<unsigned char> buf(D->pop_bytes());
+    cudaError_t e = cudaMemcpyAsync(buf.data(), D->d_pop[D->cur], buf.size(), cudaMemcpyDeviceToHost, D->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading populations");
+    CheckpointHeader H{};
+    std::memcpy(H.magic, kMagic, 8);
+    H.version = 1;
+    H.nx = D->nx;
+    H.ny = D->ny;
+    H.nz = D->nz;
+    H.storage = D->params.storage;
+    H.n_slots = D->n_slots;
+    H.time = D->time;
+    H.geometry_hash = D->geometry_hash;
+    H.params = D->params;
+    H.has_wave = D->has_wave ? 1 : 0;
+    H.n_harm = D->has_wave ? (int32_t)D->wave_a.size() - 1 : 0;
+    H.wave_period = D->wave_period;
+    H.wave_peak = D->wave_peak;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&H, sizeof(H), 1, f) == 1;
+    if (ok && H.has_wave) {
+        ok = std::fwrite(D->wave_a.data(), sizeof(double), D->wave_a.size(), f) == D->wave_a.size();
+        if (ok && H.n_harm > 0) ok = std::fwrite(D->wave_b.data(), sizeof(double), D->wave_b.size(), f) == D->wave_b.size();
+    }
+    if (ok) ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(LBM_ERR_IO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_domain* D, const char* path)
+{
+    g_last_error.clear();
+    if (!D || !path) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    CheckpointHeader H{};
+    bool ok = std::fread(&H, sizeof(H), 1, f) == 1;
+    if (!ok || std::memcmp(H.magic, kMagic, 8) != 0 || H.version != 1) {
+        std::fclose(f);
+        return fail(LBM_ERR_IO, "not a checkpoint of this library");
+    }
+    if (H.nx != D->nx || H.ny != D->ny || H.nz != D->nz || H.storage != D->params.storage ||
+        H.n_slots != D->n_slots || H.geometry_hash != D->geometry_hash) {
+        std::fclose(f);
+        return fail(LBM_ERR_IO, "checkpoint does not match this domain's geometry or storage");
+    }
+    std::vector<double> wa, wb;
+    if (H.has_wave) {
+        if (H.n_harm < 0 || H.n_harm > 15) {
+            std::fclose(f);
+            return fail(LBM_ERR_IO, "corrupt checkpoint");
+        }
+        wa.resize((size_t)H.n_harm + 1);
+        wb.resize((size_t)H.n_harm);
+        ok = std::fread(wa.data(), sizeof(double), wa.size(), f) == wa.size();
+        if (ok && H.n_harm > 0) ok = std::fread(wb.data(), sizeof(double), wb.size(), f) == wb.size();
+    }
+    std::vector<unsigned char> buf(D->pop_bytes());
+    if (ok) ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return fail(LBM_ERR_IO, "truncated checkpoint");
+    if (lbm_status s = check_params(H.params)) return s;
+    cudaError_t e = cudaMemcpyAsync(D->d_pop[D->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, D->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "writing populations");
+    D->params = H.params;
+    D->time = H.time;
+    if (H.has_wave) {
+        lbm_status s = lbm_set_inlet_waveform(D, wa.data(), wb.empty() ? nullptr : wb.data(), H.n_harm,
+                                              H.wave_period, H.wave_peak);
+        if (s) return s;
+    } else {
+        D->has_wave = false;
+        D->wave.clear();
+    }
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_domain* D)
+{
+    if (!D) return;
+    cudaStreamSynchronize(D->stream);
+    D->release_all();
+    delete D;
+}
+
+}  // extern "C"

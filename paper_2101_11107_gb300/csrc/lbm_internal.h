@@ -1,0 +1,76 @@
+// lbm_internal.h -- shared declarations of the CUDA library (device views, launch arguments,
+// stencil constants).  Not part of the public C-ABI (include/lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// D3Q27, i = (cx+1) + 3 (cy+1) + 9 (cz+1); opposite = 26 - i.  Weights are the products of the
+// D1Q3 weights (2/3, 1/6, 1/6): 8/27, 2/27, 1/54, 1/216 by |c|^2.
+constexpr int Q = 27;
+__host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz_of(int i) { return i / 9 - 1; }
+__host__ __device__ constexpr float w1_of(int c) { return c == 0 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+__host__ __device__ constexpr float w_of(int i)
+{
+    return w1_of(cx_of(i)) * w1_of(cy_of(i)) * w1_of(cz_of(i));
+}
+__host__ __device__ constexpr float inv_w_of(int i) { return 1.0f / w_of(i); }
+
+// Geometry is stored in 4x4x4 bricks; a population slot is brick * 64 + lx + 4 ly + 16 lz.
+constexpr int BRICK_EDGE = 4;
+constexpr int BRICK_CELLS = 64;
+constexpr int STEP_BRICKS_PER_CTA = 4;  // 256 threads per CTA in the step kernel
+
+// Per-slot cell word.
+//   bits 0..26  wall mask: bit i set <=> the pull source x - c_i is not a fluid cell
+//   bits 27..28 kind (plain / Bouzidi / inlet / outlet)
+//   bit 31      the slot is a fluid cell (updated every step); solid slots have word 0
+constexpr uint32_t WORD_FLUID = 1u << 31;
+constexpr uint32_t WORD_WALL_MASK = (1u << 27) - 1u;
+constexpr int WORD_KIND_SHIFT = 27;
+enum CellKind { KIND_PLAIN = 0, KIND_BOUZIDI = 1, KIND_INLET = 2, KIND_OUTLET = 3 };
+
+// Read-only geometry of a domain on the device.
+struct DomainView {
+    int64_t n_slots;
+    int64_t n_bricks;
+    const int32_t* nbr;     // [n_bricks][27] brick at offset (ox,oy,oz), index 13 = itself; -1 none
+    const uint32_t* word;   // [n_slots]
+    const int32_t* aux;     // [n_slots] record of a Bouzidi or open-boundary cell
+    const float* bq;        // [27][n_bq] Bouzidi q of the link whose unknown is i (0: halfway BB)
+    int64_t n_bq;
+    const float* io_phi;    // [n_io] inflow profile factor 2 (1 - r^2/R^2)
+    const int8_t* io_axis;  // [n_io] inward normal axis
+    const int8_t* io_sign;  // [n_io] inward normal sign
+    int64_t n_io;
+};
+
+// Per-launch arguments of a time level n.
+struct LevelArgs {
+    float g[3];    // body acceleration g(n)
+    float U;       // inflow U(n) for the open-boundary closure of level n
+    float s2, s3, s4, s5, s6;  // relaxation rates by moment order
+    float rho_out;
+};
+
+// Launchers (lbm_kernels.cu).  All enqueue on `stream` and return the launch status.
+cudaError_t launch_step(int storage, const DomainView& v, const void* src, void* dst,
+                        const LevelArgs& a, cudaStream_t stream);
+cudaError_t launch_macroscopic(int storage, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,
+                               int dense, float* rho, float* u, int64_t n_out, cudaStream_t stream);
+cudaError_t launch_init_equilibrium(int storage, int64_t n_slots, void* dst, const int32_t* fl_slot,
+                                    const int32_t* fl_box, int64_t n_fluid, const float* rho,
+                                    const float* u, int64_t n_box, cudaStream_t stream);
+int64_t diagnostics_blocks(int64_t n_fluid);
+cudaError_t launch_diagnostics(int storage, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, int64_t n_fluid, double* partials,
+                               lbm_diagnostics* out, cudaStream_t stream);
+
+}  // namespace lbm

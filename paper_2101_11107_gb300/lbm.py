@@ -1,0 +1,262 @@
+"""Python binding of the C-ABI in ``include/lbm.h`` (ctypes; argument marshalling only).
+
+Every step of the lattice Boltzmann path runs in the CUDA library ``_build/liblbm_gb300.so``;
+this module only converts arguments.  There is no CPU fallback: if the library is missing or
+no GPU is present, the calls raise.  PyTorch supplies device memory (the library allocates
+through callbacks backed by the caching allocator) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbm_gb300.so")
+
+STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSTABLE", 5: "TIMEOUT", 6: "STATE", 7: "IO"}
+
+# every entry point declared in include/lbm.h
+EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium",
+           "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
+           "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error"]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("omega_hi", ctypes.c_double * 4),
+                ("force", ctypes.c_double * 3), ("force_amp", ctypes.c_double * 3),
+                ("force_omega", ctypes.c_double), ("rho_out", ctypes.c_double),
+                ("periodic", ctypes.c_int32 * 3), ("storage", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_fluid", ctypes.c_int64), ("n_bricks", ctypes.c_int64), ("n_slots", ctypes.c_int64),
+                ("n_wall_cells", ctypes.c_int64), ("n_bouzidi_cells", ctypes.c_int64),
+                ("n_open_cells", ctypes.c_int64), ("time", ctypes.c_int64), ("storage", ctypes.c_int32),
+                ("bytes_per_value", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Diagnostics(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("flux_in", ctypes.c_double), ("flux_out", ctypes.c_double),
+                ("max_u", ctypes.c_double), ("n_nonfinite", ctypes.c_int64), ("time", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.lbm_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.lbm_default_params.restype = None
+    L.lbm_create_domain.argtypes = [vp, i32, i32, i32, vp, vp, vp, i64, vp, dbl, ctypes.POINTER(Params),
+                                    ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(vp)]
+    L.lbm_set_inlet_waveform.argtypes = [vp, vp, vp, i32, dbl, dbl]
+    L.lbm_init_equilibrium.argtypes = [vp, vp, vp, i32]
+    L.lbm_step.argtypes = [vp, i64]
+    L.lbm_get_macroscopic.argtypes = [vp, vp, vp, i32, i32]
+    L.lbm_get_diagnostics.argtypes = [vp, ctypes.POINTER(Diagnostics)]
+    L.lbm_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.lbm_sync.argtypes = [vp]
+    L.lbm_save_state.argtypes = [vp, ctypes.c_char_p]
+    L.lbm_load_state.argtypes = [vp, ctypes.c_char_p]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = []
+    L.lbm_last_error.restype = ctypes.c_char_p
+    for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
+                 "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
+                 "lbm_save_state", "lbm_load_state"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise LbmError(status, load_library().lbm_last_error().decode())
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class TorchAllocator:
+    """Device allocator callbacks backed by the PyTorch caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self._torch = torch
+        self._device = device
+        self._live = {}
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device=self._device)
+        except Exception:  # out of memory: report NULL to the library
+            return None
+        p = t.data_ptr()
+        self._live[p] = t
+        return p
+
+    def _free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+
+class Domain:
+    """A voxel domain on the GPU (see include/lbm.h for the semantics of each call)."""
+
+    def __init__(self, mask, periodic=(0, 0, 0), links=None, inlet_center=None, inlet_radius=0.0,
+                 tau=0.6, omega_hi=(1.0, 1.0, 1.0, 1.0), force=(0.0, 0.0, 0.0), force_amp=(0.0, 0.0, 0.0),
+                 force_omega=0.0, rho_out=1.0, storage="fp32", device=None, stream=None):
+        import torch
+        L = load_library()
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        if mask.ndim != 3:
+            raise ValueError("mask must have shape (nz, ny, nx)")
+        self.shape = mask.shape
+        nz, ny, nx = mask.shape
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        p = Params()
+        L.lbm_default_params(ctypes.byref(p))
+        p.tau = tau
+        for k in range(4):
+            p.omega_hi[k] = omega_hi[k]
+        for d in range(3):
+            p.force[d] = force[d]
+            p.force_amp[d] = force_amp[d]
+            p.periodic[d] = int(bool(periodic[d]))
+        p.force_omega = force_omega
+        p.rho_out = rho_out
+        p.storage = STORE[storage] if isinstance(storage, str) else int(storage)
+        self.storage = storage
+        if links is None or len(links[0]) == 0:
+            lc = ld = lq = None
+            n_links = 0
+        else:
+            lc = np.ascontiguousarray(links[0], dtype=np.int64)
+            ld = np.ascontiguousarray(links[1], dtype=np.uint8)
+            lq = np.ascontiguousarray(links[2], dtype=np.float64)
+            n_links = len(lc)
+        ic = None if inlet_center is None else np.ascontiguousarray(inlet_center, dtype=np.float64)
+        self._alloc = TorchAllocator(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.lbm_create_domain(_ptr(mask), nx, ny, nz, _ptr(lc), _ptr(ld), _ptr(lq), n_links, _ptr(ic),
+                                       float(inlet_radius), ctypes.byref(p), self._alloc.alloc_fn,
+                                       self._alloc.free_fn, None, ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_geometry(cls, g, storage="fp32", **kw):
+        dom = cls(g.mask, periodic=g.periodic, links=g.links, inlet_center=g.inlet_center,
+                  inlet_radius=g.inlet_radius, tau=g.tau, force=g.g0, force_amp=g.gamp,
+                  force_omega=g.gomega, storage=storage, **kw)
+        if g.wave is not None:
+            a, b, P, up = g.wave
+            dom.set_inlet_waveform(a, b, P, up)
+        return dom
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_inlet_waveform(self, a, b, period, u_peak):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        _check(load_library().lbm_set_inlet_waveform(self._h, _ptr(a), _ptr(b) if b.size else None, len(a) - 1,
+                                                      float(period), float(u_peak)))
+
+    def init_equilibrium(self, rho, u):
+        """rho (nz,ny,nx) and u (3,nz,ny,nx): numpy arrays or CUDA tensors."""
+        import torch
+        L = load_library()
+        if isinstance(rho, torch.Tensor):
+            rho_t = rho.to(torch.float32).contiguous()
+            u_t = u.to(torch.float32).contiguous()
+            _check(L.lbm_init_equilibrium(self._h, ctypes.c_void_p(rho_t.data_ptr()),
+                                          ctypes.c_void_p(u_t.data_ptr()), 1))
+        else:
+            r = np.ascontiguousarray(rho, dtype=np.float32)
+            uu = np.ascontiguousarray(u, dtype=np.float32)
+            _check(L.lbm_init_equilibrium(self._h, _ptr(r), _ptr(uu), 0))
+
+    def step(self, n=1):
+        _check(load_library().lbm_step(self._h, int(n)))
+
+    def sync(self):
+        _check(load_library().lbm_sync(self._h))
+
+    def info(self) -> dict:
+        i = Info()
+        _check(load_library().lbm_get_info(self._h, ctypes.byref(i)))
+        return i.as_dict()
+
+    @property
+    def time(self):
+        return self.info()["time"]
+
+    def macroscopic(self, dense=True):
+        """(rho, u) as numpy float32 arrays: dense (nz,ny,nx)/(3,nz,ny,nx), or compact
+        (n_fluid,)/(3,n_fluid) in increasing box order."""
+        nz, ny, nx = self.shape
+        n = nx * ny * nz if dense else self.info()["n_fluid"]
+        rho = np.empty(n, np.float32)
+        u = np.empty(3 * n, np.float32)
+        _check(load_library().lbm_get_macroscopic(self._h, _ptr(rho), _ptr(u), int(dense), 0))
+        if dense:
+            return rho.reshape(nz, ny, nx), u.reshape(3, nz, ny, nx)
+        return rho, u.reshape(3, n)
+
+    def macroscopic_device(self, rho, u, dense=True):
+        """Writes into CUDA float32 tensors on the domain's stream (no host round trip)."""
+        _check(load_library().lbm_get_macroscopic(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                                  ctypes.c_void_p(u.data_ptr()), int(dense), 1))
+
+    def diagnostics(self, raise_unstable=True) -> dict:
+        dg = Diagnostics()
+        st = load_library().lbm_get_diagnostics(self._h, ctypes.byref(dg))
+        if st != 0 and (raise_unstable or st != 4):
+            _check(st)
+        return dg.as_dict()
+
+    def save_state(self, path):
+        _check(load_library().lbm_save_state(self._h, os.fsencode(path)))
+
+    def load_state(self, path):
+        _check(load_library().lbm_load_state(self._h, os.fsencode(path)))

@@ -1,0 +1,114 @@
+"""CPU checks of the C-ABI library: it builds, loads without a GPU, exports every entry point
+declared in include/lbm.h, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2101_11107_gb300 import build as lib_build
+from paper_2101_11107_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    lib_build.build()
+    return lbm.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert set(declared_functions()) == set(lbm.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_default_params(L):
+    p = lbm.Params()
+    L.lbm_default_params(ctypes.byref(p))
+    assert p.tau == 0.6 and list(p.omega_hi) == [1.0] * 4 and p.rho_out == 1.0 and p.storage == 0
+
+
+def _create(L, mask, links=None, params=None, inlet_center=None, inlet_radius=0.0):
+    nz, ny, nx = mask.shape
+    mask = np.ascontiguousarray(mask, np.uint8)
+    p = lbm.Params()
+    L.lbm_default_params(ctypes.byref(p))
+    for k, v in (params or {}).items():
+        if k == "periodic":
+            for d in range(3):
+                p.periodic[d] = v[d]
+        else:
+            setattr(p, k, v)
+    if links is None:
+        lc = ld = lq = None
+        n = 0
+    else:
+        lc = np.ascontiguousarray(links[0], np.int64)
+        ld = np.ascontiguousarray(links[1], np.uint8)
+        lq = np.ascontiguousarray(links[2], np.float64)
+        n = len(lc)
+    ic = None if inlet_center is None else np.ascontiguousarray(inlet_center, np.float64)
+    h = ctypes.c_void_p()
+    st = L.lbm_create_domain(lbm._ptr(mask), nx, ny, nz, lbm._ptr(lc), lbm._ptr(ld), lbm._ptr(lq), n,
+                             lbm._ptr(ic), inlet_radius, ctypes.byref(p), lbm.ALLOC_FN(0), lbm.FREE_FN(0),
+                             None, None, ctypes.byref(h))
+    return st, L.lbm_last_error().decode(), h
+
+
+@pytest.mark.parametrize("case", ["mask_value", "periodic_extent", "tau", "omega", "link_not_wall",
+                                  "link_q", "link_on_inlet", "duplicate_link", "open_cell_off_face",
+                                  "inlet_without_radius"])
+def test_invalid_arguments_rejected_before_device_work(L, case):
+    mask = np.ones((4, 8, 8), np.uint8)
+    mask[:, :, 0] = 0
+    mask[:, :, -1] = 0
+    kw = {}
+    if case == "mask_value":
+        mask[1, 1, 1] = 7
+    elif case == "periodic_extent":
+        mask = np.ones((6, 8, 8), np.uint8)
+        kw["params"] = {"periodic": (1, 1, 1)}
+    elif case == "tau":
+        kw["params"] = {"tau": 0.5}
+    elif case == "omega":
+        kw["params"] = {"omega_hi": (ctypes.c_double * 4)(1.0, 2.5, 1.0, 1.0)}
+    elif case == "link_not_wall":
+        kw["links"] = ([1 + 8 * 2 + 64 * 1], [14], [0.3])  # +x neighbour of (1,2,1) is fluid
+    elif case == "link_q":
+        kw["links"] = ([1 + 8 * 2 + 64 * 1], [12], [0.0])
+    elif case == "link_on_inlet":
+        mask[:, :, 1] = 2
+        kw["links"] = ([1 + 8 * 2 + 64 * 1], [12], [0.3])
+        kw["inlet_center"] = (0.0, 4.0, 2.0)
+        kw["inlet_radius"] = 3.0
+    elif case == "duplicate_link":
+        kw["links"] = ([1 + 8 * 2 + 64 * 1] * 2, [12, 12], [0.3, 0.4])
+    elif case == "open_cell_off_face":
+        mask[2, 3, 3] = 3
+    elif case == "inlet_without_radius":
+        mask[:, :, 1] = 0
+        mask[:, :, 0] = 2
+    if case == "link_on_inlet":
+        pass
+    st, msg, h = _create(L, mask, **kw)
+    assert st == 1, (case, st, msg)
+    assert msg
+    assert not h.value
+
+
+def test_null_arguments(L):
+    assert L.lbm_step(None, 1) == 1
+    assert L.lbm_sync(None) == 1
+    L.lbm_destroy(None)

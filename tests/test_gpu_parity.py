@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the same seeded
+inputs, element by element.
+
+Tolerance (FP32 storage and arithmetic): max_x |u_gpu - u_ref| / max_x |u_ref| <= 1e-5 after up
+to 1000 steps, and |rho_gpu - rho_ref| <= 1e-5; normalising by the field maximum because
+pointwise relative error is undefined at rest and near walls.  16-bit storage keeps FP32
+arithmetic and rounds the stored (f - w)/w to 11 (FP16) or 8 (BF16) significant bits per step;
+its bound is derived in the test from that rounding.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_11107_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2101_11107_gb300 import lbm  # noqa: E402
+
+oracle.set_threads(min(16, os.cpu_count() or 1))
+FP32_TOL = 1e-5
+
+
+def run_pair(g, steps, storage="fp32", init=None, ref_mask=None):
+    """Advance the GPU domain and the oracle on geometry g; return both macroscopic fields.
+    ref_mask: optional smaller z-slab for the oracle (translational invariance)."""
+    dom = lbm.Domain.from_geometry(g, storage=storage)
+    rm = g.mask if ref_mask is None else ref_mask
+    links = g.links if ref_mask is None else None
+    ref = oracle.Case(rm, periodic=g.periodic, links=links, inlet_center=g.inlet_center,
+                      inlet_radius=g.inlet_radius, tau=g.tau, g0=g.g0, gamp=g.gamp, gomega=g.gomega)
+    if g.wave is not None:
+        ref.set_waveform(*g.wave)
+    if init is not None:
+        rho0, u0 = init
+        dom.init_equilibrium(rho0, u0)
+        ref.init_equilibrium(rho0[: rm.shape[0]], u0[:, : rm.shape[0]])
+    dom.step(steps)
+    ref.step(steps)
+    rho, u = dom.macroscopic()
+    rho_r, u_r = ref.macroscopic()
+    info = dom.info()
+    dom.close()
+    assert info["time"] == steps == ref.time
+    return rho, u, rho_r, u_r
+
+
+def rel_u(u, u_r):
+    return float(np.abs(u - u_r).max() / np.abs(u_r).max())
+
+
+def test_poiseuille_pipe_config_full_size():
+    """Radius-12 pipe, 32x32x64 periodic in z, tau 0.6, g 1e-6, halfway bounce-back, 1000 steps:
+    every z-layer of the GPU field against the oracle's one-layer slab."""
+    g = I.poiseuille_pipe_32()
+    rho, u, rho_r, u_r = run_pair(g, 1000, ref_mask=g.mask[:1].copy())
+    for z in range(g.mask.shape[0]):
+        assert rel_u(u[:, z:z + 1], u_r) <= FP32_TOL, z
+        assert np.abs(rho[z] - rho_r[0]).max() <= 1e-5
+
+
+def test_taylor_green_init_equilibrium():
+    """Periodic 32x32x4 Taylor-Green vortex from an equilibrium initial state, 400 steps."""
+    rho0, u0 = I.taylor_green(32, 32, 4, 0.02)
+    g = I.Geometry(mask=np.ones((4, 32, 32), np.uint8), periodic=(1, 1, 1), tau=0.7)
+    rho, u, rho_r, u_r = run_pair(g, 400, init=(rho0, u0), ref_mask=np.ones((1, 32, 32), np.uint8))
+    for z in range(4):
+        assert rel_u(u[:, z:z + 1], u_r) <= FP32_TOL
+    assert np.abs(rho[0] - rho_r[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("omega_hi", [(1.0, 1.0, 1.0, 1.0)])
+def test_bouzidi_pipe(omega_hi):
+    """Exact-q Bouzidi walls (both branches, tie-breaks) on a radius-9.3 pipe, 600 steps."""
+    g = I.pipe(24, 24, 8, 9.3, center=(12.2, 11.9), tau=0.56, g0=(0.0, 0.0, 2e-6), bouzidi=True)
+    rho, u, rho_r, u_r = run_pair(g, 600)
+    assert rel_u(u, u_r) <= FP32_TOL
+    assert np.abs(rho - rho_r).max() <= 1e-5
+
+
+def test_open_boundaries_pulsatile():
+    """Velocity inlet with a seeded 5-harmonic waveform (period 300 steps) and density
+    outlet on a pipe along x, 600 steps."""
+    g = I.inlet_pipe(32, 12, 12, 4.7, u_peak=0.02, tau=0.6)
+    g.wave = I.cardiac_waveform(3, period=300.0, u_peak=0.02)
+    rho, u, rho_r, u_r = run_pair(g, 600)
+    assert rel_u(u, u_r) <= FP32_TOL
+    assert np.abs(rho - rho_r).max() <= 1e-5
+
+
+@pytest.mark.parametrize("seed,edge", [(1, 64), (7, 96)])
+def test_synthetic_aneurysm_downscaled(seed, edge):
+    """The seeded aneurysm generator at a reduced box (all boundary kinds at once: Bouzidi
+    walls, inlet waveform, outlet), 400 steps, every cell."""
+    g = I.aneurysm(seed, edge=edge, period=400.0)
+    rho, u, rho_r, u_r = run_pair(g, 400)
+    assert rel_u(u, u_r) <= FP32_TOL
+    assert np.abs(rho - rho_r).max() <= 1e-5
+
+
+def test_empty_and_ragged_boxes():
+    """A box whose extents are not multiples of the 4^3 brick (ragged bricks), one with no
+    fluid at all, and a single fluid cell."""
+    mask = np.zeros((7, 9, 11), np.uint8)
+    mask[1:6, 2:8, 1:10] = 1
+    g = I.Geometry(mask=mask, tau=0.9, g0=(1e-5, 2e-5, -1e-5))
+    rho, u, rho_r, u_r = run_pair(g, 100)
+    assert rel_u(u, u_r) <= FP32_TOL
+    empty = I.Geometry(mask=np.zeros((5, 5, 5), np.uint8))
+    dom = lbm.Domain.from_geometry(empty)
+    dom.step(3)
+    rho, u = dom.macroscopic()
+    assert np.all(rho == 0) and dom.info()["n_fluid"] == 0
+    one = np.zeros((3, 3, 3), np.uint8)
+    one[1, 1, 1] = 1
+    dom = lbm.Domain.from_geometry(I.Geometry(mask=one, g0=(1e-4, 0, 0)))
+    dom.step(10)
+    rho, u = dom.macroscopic()
+    assert abs(rho[1, 1, 1] - 1.0) < 1e-6
+
+
+def test_womersley_full_size_fp32():
+    """Womersley configuration at full size (64x64x256, R 28, tau 0.55, Wo 4, amplitude 1e-5)
+    for 1000 steps in the launch configuration the benchmark times, against the oracle's
+    z-slab (the flow is z-invariant)."""
+    g = I.womersley_pipe()
+    rho, u, rho_r, u_r = run_pair(g, 1000, ref_mask=g.mask[:1].copy())
+    for z in range(0, 256, 17):
+        assert rel_u(u[:, z:z + 1], u_r) <= FP32_TOL
+
+
+@pytest.mark.parametrize("storage,bound", [("fp16", 3e-3), ("bf16", 2.5e-2)])
+def test_sixteen_bit_storage_error(storage, bound):
+    """16-bit deviation storage, FP32 arithmetic: the error against the FP64 oracle stays within
+    the bound set by one rounding of (f - w)/w per step (2^-11 FP16, 2^-8 BF16) accumulated
+    over the relaxation memory of the flow."""
+    g = I.pipe(32, 32, 4, 12.0, center=(16.0, 16.0), tau=0.6, g0=(0.0, 0.0, 1e-5), bouzidi=True)
+    rho, u, rho_r, u_r = run_pair(g, 1000, storage=storage)
+    fl = g.mask > 0
+    e = np.linalg.norm(u[:, fl] - u_r[:, fl]) / np.linalg.norm(u_r[:, fl])
+    assert e <= bound, e
+
+
+def test_mass_conserved_and_diagnostics():
+    """Closed periodic + bounce-back pipe: FP64 mass reduction stays constant to FP32 round-off;
+    diagnostics are reproducible bit for bit."""
+    g = I.poiseuille_pipe_32()
+    dom = lbm.Domain.from_geometry(g)
+    d0 = dom.diagnostics()
+    dom.step(500)
+    d1 = dom.diagnostics()
+    d1b = dom.diagnostics()
+    assert d1 == d1b
+    n = dom.info()["n_fluid"]
+    assert abs(d0["mass"] - n) < 1e-9
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-6
+    assert d1["n_nonfinite"] == 0 and d1["max_u"] > 0
+
+
+def test_open_boundary_flux_diagnostics():
+    g = I.inlet_pipe(32, 12, 12, 4.7, u_peak=0.02, tau=0.6)
+    dom = lbm.Domain.from_geometry(g)
+    dom.step(4000)
+    d = dom.diagnostics()
+    assert d["flux_in"] > 0 and abs(d["flux_out"] / d["flux_in"] - 1.0) < 2e-2
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """N steps == k steps + save + load into a fresh domain + (N - k) steps, bit for bit."""
+    g = I.aneurysm(2, edge=64, period=200.0)
+    a = lbm.Domain.from_geometry(g)
+    a.step(120)
+    rho_a, u_a = a.macroscopic()
+    b = lbm.Domain.from_geometry(g)
+    b.step(50)
+    b.save_state(tmp_path / "ck.bin")
+    c = lbm.Domain.from_geometry(g)
+    c.load_state(tmp_path / "ck.bin")
+    assert c.time == 50
+    c.step(70)
+    rho_c, u_c = c.macroscopic()
+    assert np.array_equal(rho_a, rho_c) and np.array_equal(u_a, u_c)
+
+
+def test_compact_export_matches_dense():
+    g = I.aneurysm(4, edge=64)
+    dom = lbm.Domain.from_geometry(g)
+    dom.step(20)
+    rho, u = dom.macroscopic(dense=True)
+    rc, uc = dom.macroscopic(dense=False)
+    fl = g.mask.reshape(-1) > 0
+    assert np.array_equal(rho.reshape(-1)[fl], rc)
+    assert np.array_equal(u.reshape(3, -1)[:, fl], uc)
