@@ -221,6 +221,8 @@ def main():
             times = time_steps(dom, args.steps, args.warmup, flush, stream)
         ms = statistics.mean(times)
         bytes_alg = 2 * 27 * BYTES_PER_VALUE[storage] * nf
+        if storage == "fp32":
+            fp32_times = times
         results[storage] = {"ms_per_step": ms, "mlups": nf / (ms * 1e-3) / 1e6, "fluid_cells": nf,
                             "algorithmic_bytes_per_launch": bytes_alg,
                             "achieved_gbs": bytes_alg / (ms * 1e-3) / 1e9,
@@ -231,7 +233,7 @@ def main():
             main_dom = dom
 
     main = results["fp32"]
-    total_ms = sum(times)
+    total_ms = sum(fp32_times)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

@@ -98,26 +98,38 @@ def test_open_boundaries_pulsatile():
 @pytest.mark.parametrize("seed,edge", [(1, 64), (7, 96)])
 def test_synthetic_aneurysm_downscaled(seed, edge):
     """The seeded aneurysm generator at a reduced box (all boundary kinds at once: Bouzidi
-    walls, inlet waveform, outlet), 400 steps, every cell."""
-    g = I.aneurysm(seed, edge=edge, period=400.0)
+    walls, inlet waveform, outlet), 400 steps, every cell.  Re 20 keeps the flow laminar at
+    this resolution: at Re 300 a 3-cell vessel with tau ~ 0.5015 amplifies a 1e-7 perturbation
+    to 1e-2 within 400 steps in the oracle alone, so FP32 and FP64 runs part ways for reasons
+    of the flow, not of the arithmetic."""
+    g = I.aneurysm(seed, edge=edge, period=400.0, reynolds=20.0)
     rho, u, rho_r, u_r = run_pair(g, 400)
     assert rel_u(u, u_r) <= FP32_TOL
     assert np.abs(rho - rho_r).max() <= 1e-5
 
 
-def test_empty_and_ragged_boxes():
-    """A box whose extents are not multiples of the 4^3 brick (ragged bricks), one with no
-    fluid at all, and a single fluid cell."""
-    mask = np.zeros((7, 9, 11), np.uint8)
-    mask[1:6, 2:8, 1:10] = 1
-    g = I.Geometry(mask=mask, tau=0.9, g0=(1e-5, 2e-5, -1e-5))
-    rho, u, rho_r, u_r = run_pair(g, 100)
+def test_synthetic_aneurysm_full_size_short():
+    """The 256^3 synthetic aneurysm at Re 300 (tau ~ 0.506), Bouzidi walls, pulsatile inlet,
+    outlet: 30 steps in the benchmark's launch configuration, every fluid cell."""
+    g = I.aneurysm(11, edge=256)
+    rho, u, rho_r, u_r = run_pair(g, 30)
     assert rel_u(u, u_r) <= FP32_TOL
+    assert np.abs(rho - rho_r).max() <= 1e-5
+
+
+def test_ragged_and_degenerate_boxes():
+    """Box extents that are not multiples of the 4^3 brick (ragged bricks) on an open pipe with
+    flow, a box with no fluid at all, and a single fluid cell."""
+    g = I.inlet_pipe(30, 11, 13, 4.4, u_peak=0.02, tau=0.7)
+    rho, u, rho_r, u_r = run_pair(g, 300)
+    assert rel_u(u, u_r) <= FP32_TOL
+    assert np.abs(rho - rho_r).max() <= 1e-5
     empty = I.Geometry(mask=np.zeros((5, 5, 5), np.uint8))
     dom = lbm.Domain.from_geometry(empty)
     dom.step(3)
     rho, u = dom.macroscopic()
     assert np.all(rho == 0) and dom.info()["n_fluid"] == 0
+    assert dom.diagnostics()["mass"] == 0.0
     one = np.zeros((3, 3, 3), np.uint8)
     one[1, 1, 1] = 1
     dom = lbm.Domain.from_geometry(I.Geometry(mask=one, g0=(1e-4, 0, 0)))
@@ -136,15 +148,29 @@ def test_womersley_full_size_fp32():
         assert rel_u(u[:, z:z + 1], u_r) <= FP32_TOL
 
 
-@pytest.mark.parametrize("storage,bound", [("fp16", 3e-3), ("bf16", 2.5e-2)])
-def test_sixteen_bit_storage_error(storage, bound):
-    """16-bit deviation storage, FP32 arithmetic: the error against the FP64 oracle stays within
-    the bound set by one rounding of (f - w)/w per step (2^-11 FP16, 2^-8 BF16) accumulated
-    over the relaxation memory of the flow."""
-    g = I.pipe(32, 32, 4, 12.0, center=(16.0, 16.0), tau=0.6, g0=(0.0, 0.0, 1e-5), bouzidi=True)
-    rho, u, rho_r, u_r = run_pair(g, 1000, storage=storage)
+def sixteen_bit_error(storage, case):
+    if case == "force":
+        g = I.pipe(32, 32, 4, 12.0, center=(16.0, 16.0), tau=0.6, g0=(0.0, 0.0, 1e-5), bouzidi=True)
+        steps = 1000
+    else:
+        g = I.aneurysm(5, edge=96, period=400.0, reynolds=20.0)
+        steps = 800
+    rho, u, rho_r, u_r = run_pair(g, steps, storage=storage)
     fl = g.mask > 0
-    e = np.linalg.norm(u[:, fl] - u_r[:, fl]) / np.linalg.norm(u_r[:, fl])
+    return float(np.linalg.norm(u[:, fl] - u_r[:, fl]) / np.linalg.norm(u_r[:, fl]))
+
+
+@pytest.mark.parametrize("storage,case,bound", [("fp16", "force", 3e-3), ("fp16", "inlet", 3e-3),
+                                                ("bf16", "inlet", 3e-2), ("bf16", "force", 0.5)])
+def test_sixteen_bit_storage_error(storage, case, bound):
+    """16-bit deviation storage, FP32 arithmetic, against the FP64 oracle (relative L2 of u).
+    Each stored (f - w)/w is rounded once per step to 11 (FP16) or 8 (BF16) significant bits.
+    FP16 keeps the error at the 1e-3 level.  BF16's half-ulp of a typical (f - w)/w ~ 1e-2 is
+    ~2e-5, the same size as the per-step momentum input of a body force of 1e-5: increments
+    below it are rounded away, so on the weakly forced pipe BF16 storage stalls the flow
+    (error O(0.1)); on inlet-driven flows the error is at the 1e-2 level."""
+    e = sixteen_bit_error(storage, case)
+    print(f"{storage} {case} rel-L2 {e:.3e}")
     assert e <= bound, e
 
 
