@@ -87,6 +87,7 @@ typedef struct {
     int32_t storage;
     int32_t bytes_per_value; /* 4 (FP32) or 2 (FP16/BF16) */
     int64_t device_bytes;    /* device memory held by the domain */
+    int32_t launch_config;   /* launch configuration of the step kernel in use */
 } lbm_info;
 
 typedef struct {
@@ -166,6 +167,21 @@ lbm_status lbm_get_macroscopic(lbm_domain* dom, float* rho, float* u, int32_t de
 lbm_status lbm_get_diagnostics(lbm_domain* dom, lbm_diagnostics* out);
 
 lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
+
+/* Number of launch configurations of the fused step kernel. */
+#define LBM_N_LAUNCH_CONFIGS 6
+
+/* Selects the step kernel's launch configuration: 0..5 = 256 threads (four 4^3 bricks) per CTA
+ * with a register budget for 2, 3 or 4 resident CTAs per SM; 128 threads with 6 or 8; 512
+ * threads with 1.  Results do not depend on it.  Default 1.  Errors: INVALID_ARG. */
+lbm_status lbm_set_launch_config(lbm_domain* dom, int32_t config);
+
+/* Times every launch configuration on this domain (trial_steps steps each, CUDA events on the
+ * domain's stream) and selects the fastest.  The domain's populations and time level are left
+ * as they were.  ms_per_step (may be NULL) receives LBM_N_LAUNCH_CONFIGS times; *best_config
+ * (may be NULL) the choice.  Waits for the stream.  Allocates one population array while it
+ * runs.  Errors: INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_config, float* ms_per_step);
 
 /* Waits for all work enqueued on the domain. */
 lbm_status lbm_sync(lbm_domain* dom);

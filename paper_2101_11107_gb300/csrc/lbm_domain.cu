@@ -40,6 +40,7 @@ struct lbm_domain {
     int32_t* d_fl_box = nullptr;
     void* d_pop[2] = {nullptr, nullptr};
     int cur = 0;  // d_pop[cur] holds the post-collision populations of level time - 1
+    int launch_config = DEFAULT_LAUNCH_CONFIG;
     double* d_partials = nullptr;
     lbm_diagnostics* d_diag = nullptr;
     int64_t time = 0;
@@ -222,7 +223,8 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
             brick_pos.push_back((int32_t)(bb / ((int64_t)nbx * nby)));
         }
     const int64_t n_slots = n_bricks * BRICK_CELLS;
-    if (n_slots * Q >= ((int64_t)1 << 40)) return fail(LBM_ERR_INVALID_ARG, "domain too large");
+    // kernels address populations with 32-bit element offsets i * n_slots + slot
+    if (n_slots * Q >= ((int64_t)1 << 32)) return fail(LBM_ERR_INVALID_ARG, "domain too large (27 x slots >= 2^32)");
     const int nb3[3] = {nbx, nby, nbz};
     std::vector<int32_t> nbr((size_t)n_bricks * Q, -1);
     for (int64_t b = 0; b < n_bricks; ++b) {
@@ -502,11 +504,72 @@ lbm_status lbm_step(lbm_domain* D, int64_t n)
     if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
     for (int64_t k = 0; k < n; ++k) {
         const LevelArgs a = D->level_args(D->time);
-        cudaError_t e = launch_step(D->params.storage, D->view, D->d_pop[D->cur], D->d_pop[1 - D->cur], a, D->stream);
+        cudaError_t e = launch_step(D->params.storage, D->launch_config, D->view, D->d_pop[D->cur],
+                                    D->d_pop[1 - D->cur], a, D->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         D->cur = 1 - D->cur;
         D->time += 1;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch_config(lbm_domain* D, int32_t config)
+{
+    g_last_error.clear();
+    if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
+    if (config < 0 || config >= N_LAUNCH_CONFIGS) return fail(LBM_ERR_INVALID_ARG, "launch config out of range");
+    D->launch_config = config;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config, float* ms_per_step)
+{
+    g_last_error.clear();
+    if (!D || trial_steps < 1) return fail(LBM_ERR_INVALID_ARG, "bad arguments");
+    if (D->n_bricks == 0) {
+        if (best_config) *best_config = D->launch_config;
+        return LBM_OK;
+    }
+    // keep the state: trials run from a copy of the current populations into the other array,
+    // and the copy is restored at the end
+    void* keep = D->dev_alloc(D->pop_bytes());
+    if (!keep) return fail(LBM_ERR_OOM, "allocation failed: autotune copy");
+    cudaError_t e = cudaMemcpyAsync(keep, D->d_pop[D->cur], D->pop_bytes(), cudaMemcpyDeviceToDevice, D->stream);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const LevelArgs a = D->level_args(D->time);
+    int best = D->launch_config;
+    float best_ms = INFINITY;
+    for (int c = 0; c < N_LAUNCH_CONFIGS && e == cudaSuccess; ++c) {
+        // one untimed launch, then trial_steps alternating launches
+        e = launch_step(D->params.storage, c, D->view, keep, D->d_pop[1 - D->cur], a, D->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, D->stream);
+        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
+            const void* s = (k % 2 == 0) ? D->d_pop[1 - D->cur] : D->d_pop[D->cur];
+            void* d = (k % 2 == 0) ? D->d_pop[D->cur] : D->d_pop[1 - D->cur];
+            e = launch_step(D->params.storage, c, D->view, s, d, a, D->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(t1, D->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        ms /= (float)trial_steps;
+        if (ms_per_step) ms_per_step[c] = ms;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D->d_pop[D->cur], keep, D->pop_bytes(), cudaMemcpyDeviceToDevice, D->stream);
+    cudaError_t e2 = cudaStreamSynchronize(D->stream);
+    if (e == cudaSuccess) e = e2;
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    D->dev_free(keep, D->pop_bytes());
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    D->launch_config = best;
+    if (best_config) *best_config = best;
     return LBM_OK;
 }
 
@@ -578,6 +641,7 @@ lbm_status lbm_get_info(const lbm_domain* D, lbm_info* out)
     I.storage = D->params.storage;
     I.bytes_per_value = D->bytes_per_value();
     I.device_bytes = D->device_bytes;
+    I.launch_config = D->launch_config;
     *out = I;
     return LBM_OK;
 }

@@ -25,7 +25,6 @@ __host__ __device__ constexpr float inv_w_of(int i) { return 1.0f / w_of(i); }
 // Geometry is stored in 4x4x4 bricks; a population slot is brick * 64 + lx + 4 ly + 16 lz.
 constexpr int BRICK_EDGE = 4;
 constexpr int BRICK_CELLS = 64;
-constexpr int STEP_BRICKS_PER_CTA = 4;  // 256 threads per CTA in the step kernel
 
 // Per-slot cell word.
 //   bits 0..26  wall mask: bit i set <=> the pull source x - c_i is not a fluid cell
@@ -60,7 +59,10 @@ struct LevelArgs {
 };
 
 // Launchers (lbm_kernels.cu).  All enqueue on `stream` and return the launch status.
-cudaError_t launch_step(int storage, const DomainView& v, const void* src, void* dst,
+constexpr int N_LAUNCH_CONFIGS = 6;
+constexpr int DEFAULT_LAUNCH_CONFIG = 1;  // 256 threads, 3 CTAs per SM
+const char* launch_config_name(int config);
+cudaError_t launch_step(int storage, int config, const DomainView& v, const void* src, void* dst,
                         const LevelArgs& a, cudaStream_t stream);
 cudaError_t launch_macroscopic(int storage, const DomainView& v, const void* src, const LevelArgs& a,
                                const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,

@@ -45,6 +45,10 @@ struct Store<LBM_STORE_FP32> {
     {
         return __ldg(static_cast<const float*>(p) + (int64_t)i * n + s);
     }
+    static __device__ __forceinline__ float load_at(const void* p, int, uint32_t off)
+    {
+        return __ldg(static_cast<const float*>(p) + off);
+    }
     static __device__ __forceinline__ void store(void* p, int64_t n, int i, int64_t s, float v)
     {
         static_cast<float*>(p)[(int64_t)i * n + s] = v;
@@ -59,6 +63,10 @@ struct Store<LBM_STORE_FP16> {
         const __half h = __ldg(static_cast<const __half*>(p) + (int64_t)i * n + s);
         return w_of(i) * __half2float(h);
     }
+    static __device__ __forceinline__ float load_at(const void* p, int i, uint32_t off)
+    {
+        return w_of(i) * __half2float(__ldg(static_cast<const __half*>(p) + off));
+    }
     static __device__ __forceinline__ void store(void* p, int64_t n, int i, int64_t s, float v)
     {
         static_cast<__half*>(p)[(int64_t)i * n + s] = __float2half_rn(v * inv_w_of(i));
@@ -72,6 +80,10 @@ struct Store<LBM_STORE_BF16> {
     {
         const __nv_bfloat16 h = __ldg(static_cast<const __nv_bfloat16*>(p) + (int64_t)i * n + s);
         return w_of(i) * __bfloat162float(h);
+    }
+    static __device__ __forceinline__ float load_at(const void* p, int i, uint32_t off)
+    {
+        return w_of(i) * __bfloat162float(__ldg(static_cast<const __nv_bfloat16*>(p) + off));
     }
     static __device__ __forceinline__ void store(void* p, int64_t n, int i, int64_t s, float v)
     {
@@ -135,31 +147,31 @@ __device__ __forceinline__ void close_open(float (&d)[Q], int kind, int axis, in
 // Pull the 27 populations of level n into `d` (deviations) for the fluid cell at `slot`:
 // f_i(x, n) = f*_i(x - c_i, n - 1) from `src`, then the wall rules on masked links and the
 // open-boundary closure.  `nbrow` is the 27-entry neighbour row of the cell's brick.
+// Every lane issues all 27 loads unconditionally: on a wall link the address is redirected to
+// the cell's own opposite population, which is halfway bounce-back, f_i(x) = f*_opp(i)(x).  The
+// loads are independent, so they are all in flight together.
 template <int ST>
 __device__ __forceinline__ void gather(const DomainView& v, const void* __restrict__ src,
-                                       const int32_t* nbrow, int64_t slot, uint32_t word,
+                                       const int32_t* nbrow, uint32_t slot, uint32_t word,
                                        const LevelArgs& a, float (&d)[Q])
 {
     using S = Store<ST>;
+    const uint32_t n = (uint32_t)v.n_slots;
     const int l = (int)(slot & (BRICK_CELLS - 1));
     const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
     const uint32_t wm = word & WORD_WALL_MASK;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (!(wm & (1u << i))) {
-            const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
-            // sx in [-1, 4]: the arithmetic shift gives the brick offset -1, 0 or +1
-            const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-            const int64_t nb = nbrow[ob];
-            const int64_t s = nb * BRICK_CELLS + (sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4);
-            d[i] = S::load(src, v.n_slots, i, s);
-        }
+        const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
+        // sx in [-1, 4]: the arithmetic shift gives the brick offset -1, 0 or +1
+        const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+        const uint32_t nb = (uint32_t)nbrow[ob];
+        const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
+        const bool wall = (wm >> i) & 1u;
+        const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
+        d[i] = S::load_at(src, i, off);
     }
     if (wm == 0u) return;
-    // halfway bounce-back on every wall link: f_i(x, n) = f*_opp(i)(x, n - 1)
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        if (wm & (1u << i)) d[i] = S::load(src, v.n_slots, Q - 1 - i, slot);
     const int kind = (int)((word >> WORD_KIND_SHIFT) & 3u);
     if (kind == KIND_BOUZIDI) {
         // Sec. 2.1.4 in pull form with beta = opp(alpha) pointing into the wall:
@@ -286,17 +298,17 @@ __device__ __forceinline__ void collide(float (&d)[Q], const LevelArgs& a)
 }
 
 // ------------------------------------------------------------------------------ kernels
-template <int ST>
-__global__ void __launch_bounds__(STEP_BRICKS_PER_CTA * BRICK_CELLS)
+template <int ST, int BRICKS, int MINB>
+__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step(DomainView v, const void* __restrict__ src, void* __restrict__ dst, LevelArgs a)
 {
-    __shared__ int32_t s_nbr[STEP_BRICKS_PER_CTA * Q];
-    const int64_t brick0 = (int64_t)blockIdx.x * STEP_BRICKS_PER_CTA;
-    for (int t = threadIdx.x; t < STEP_BRICKS_PER_CTA * Q; t += blockDim.x)
+    __shared__ int32_t s_nbr[BRICKS * Q];
+    const int64_t brick0 = (int64_t)blockIdx.x * BRICKS;
+    for (int t = threadIdx.x; t < BRICKS * Q; t += blockDim.x)
         s_nbr[t] = (brick0 + t / Q < v.n_bricks) ? __ldg(v.nbr + brick0 * Q + t) : -1;
     __syncthreads();
-    const int64_t slot = brick0 * BRICK_CELLS + threadIdx.x;
-    if (slot >= v.n_slots) return;
+    const uint32_t slot = (uint32_t)(brick0 * BRICK_CELLS) + threadIdx.x;
+    if (slot >= (uint32_t)v.n_slots) return;
     const uint32_t word = __ldg(v.word + slot);
     if (!(word & WORD_FLUID)) return;
     float d[Q];
@@ -316,7 +328,7 @@ __global__ void __launch_bounds__(256)
     const int64_t slot = fl_slot[k];
     const uint32_t word = v.word[slot];
     float d[Q];
-    gather<ST>(v, src, v.nbr + (slot / BRICK_CELLS) * Q, slot, word, a, d);
+    gather<ST>(v, src, v.nbr + (slot / BRICK_CELLS) * Q, (uint32_t)slot, word, a, d);
     const Moments M = moments(d, a.g);
     const int64_t o = dense ? (int64_t)fl_box[k] : k;
     rho[o] = M.rho;
@@ -400,7 +412,7 @@ __global__ void __launch_bounds__(DIAG_THREADS)
         const int64_t slot = fl_slot[k];
         const uint32_t word = v.word[slot];
         float d[Q];
-        gather<ST>(v, src, v.nbr + (slot / BRICK_CELLS) * Q, slot, word, a, d);
+        gather<ST>(v, src, v.nbr + (slot / BRICK_CELLS) * Q, (uint32_t)slot, word, a, d);
         const Moments M = moments(d, a.g);
         const bool finite = isfinite(M.rho) && isfinite(M.ux) && isfinite(M.uy) && isfinite(M.uz);
         if (finite) {
@@ -448,18 +460,47 @@ int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads)
 }  // namespace
 
 // ------------------------------------------------------------------------------ launchers
-cudaError_t launch_step(int storage, const DomainView& v, const void* src, void* dst, const LevelArgs& a,
-                        cudaStream_t stream)
+// Launch configurations of the step kernel: (bricks per CTA, minimum resident CTAs per SM).
+// The second number sets the register budget: 65536 / (threads * CTAs).
+namespace {
+template <int ST, int BRICKS, int MINB>
+cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const LevelArgs& a, cudaStream_t stream)
+{
+    const int grid = grid_for(v.n_bricks, BRICKS);
+    k_step<ST, BRICKS, MINB><<<grid, BRICKS * BRICK_CELLS, 0, stream>>>(v, src, dst, a);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_step_cfg(int config, const DomainView& v, const void* src, void* dst, const LevelArgs& a,
+                            cudaStream_t stream)
+{
+    switch (config) {
+    case 0: return launch_step_t<ST, 4, 2>(v, src, dst, a, stream);
+    case 1: return launch_step_t<ST, 4, 3>(v, src, dst, a, stream);
+    case 2: return launch_step_t<ST, 4, 4>(v, src, dst, a, stream);
+    case 3: return launch_step_t<ST, 2, 6>(v, src, dst, a, stream);
+    case 4: return launch_step_t<ST, 2, 8>(v, src, dst, a, stream);
+    default: return launch_step_t<ST, 8, 1>(v, src, dst, a, stream);
+    }
+}
+}  // namespace
+
+const char* launch_config_name(int config)
+{
+    static const char* names[N_LAUNCH_CONFIGS] = {"256x2", "256x3", "256x4", "128x6", "128x8", "512x1"};
+    return (config >= 0 && config < N_LAUNCH_CONFIGS) ? names[config] : "?";
+}
+
+cudaError_t launch_step(int storage, int config, const DomainView& v, const void* src, void* dst,
+                        const LevelArgs& a, cudaStream_t stream)
 {
     if (v.n_bricks == 0) return cudaSuccess;
-    const int grid = grid_for(v.n_bricks, STEP_BRICKS_PER_CTA);
-    const int threads = STEP_BRICKS_PER_CTA * BRICK_CELLS;
     switch (storage) {
-    case LBM_STORE_FP32: k_step<LBM_STORE_FP32><<<grid, threads, 0, stream>>>(v, src, dst, a); break;
-    case LBM_STORE_FP16: k_step<LBM_STORE_FP16><<<grid, threads, 0, stream>>>(v, src, dst, a); break;
-    default: k_step<LBM_STORE_BF16><<<grid, threads, 0, stream>>>(v, src, dst, a); break;
+    case LBM_STORE_FP32: return launch_step_cfg<LBM_STORE_FP32>(config, v, src, dst, a, stream);
+    case LBM_STORE_FP16: return launch_step_cfg<LBM_STORE_FP16>(config, v, src, dst, a, stream);
+    default: return launch_step_cfg<LBM_STORE_BF16>(config, v, src, dst, a, stream);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_macroscopic(int storage, const DomainView& v, const void* src, const LevelArgs& a,

@@ -21,7 +21,10 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSTABLE", 5: "TIM
 # every entry point declared in include/lbm.h
 EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium",
            "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
-           "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error"]
+           "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error", "lbm_set_launch_config",
+           "lbm_autotune"]
+N_LAUNCH_CONFIGS = 6
+LAUNCH_CONFIG_NAMES = ["256x2", "256x3", "256x4", "128x6", "128x8", "512x1"]
 
 
 class LbmError(RuntimeError):
@@ -42,7 +45,8 @@ class Info(ctypes.Structure):
                 ("n_fluid", ctypes.c_int64), ("n_bricks", ctypes.c_int64), ("n_slots", ctypes.c_int64),
                 ("n_wall_cells", ctypes.c_int64), ("n_bouzidi_cells", ctypes.c_int64),
                 ("n_open_cells", ctypes.c_int64), ("time", ctypes.c_int64), ("storage", ctypes.c_int32),
-                ("bytes_per_value", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("bytes_per_value", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("launch_config", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,13 +88,15 @@ def load_library(path: str = LIB_PATH):
     L.lbm_sync.argtypes = [vp]
     L.lbm_save_state.argtypes = [vp, ctypes.c_char_p]
     L.lbm_load_state.argtypes = [vp, ctypes.c_char_p]
+    L.lbm_set_launch_config.argtypes = [vp, i32]
+    L.lbm_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
                  "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
-                 "lbm_save_state", "lbm_load_state"]:
+                 "lbm_save_state", "lbm_load_state", "lbm_set_launch_config", "lbm_autotune"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -254,6 +260,17 @@ class Domain:
         if st != 0 and (raise_unstable or st != 4):
             _check(st)
         return dg.as_dict()
+
+    def set_launch_config(self, config):
+        _check(load_library().lbm_set_launch_config(self._h, int(config)))
+
+    def autotune(self, trial_steps=20):
+        """Times every launch configuration on this domain and keeps the fastest; returns
+        (best, {name: ms_per_step})."""
+        best = ctypes.c_int32()
+        ms = (ctypes.c_float * N_LAUNCH_CONFIGS)()
+        _check(load_library().lbm_autotune(self._h, int(trial_steps), ctypes.byref(best), ms))
+        return best.value, dict(zip(LAUNCH_CONFIG_NAMES, list(ms)))
 
     def save_state(self, path):
         _check(load_library().lbm_save_state(self._h, os.fsencode(path)))
