@@ -112,6 +112,7 @@ struct lbm_domain {
         a.s5 = (float)params.omega_hi[2];
         a.s6 = (float)params.omega_hi[3];
         a.rho_out = (float)params.rho_out;
+        a.drho_out = (float)(params.rho_out - 1.0);
         return a;
     }
 };

@@ -56,6 +56,7 @@ struct LevelArgs {
     float U;       // inflow U(n) for the open-boundary closure of level n
     float s2, s3, s4, s5, s6;  // relaxation rates by moment order
     float rho_out;
+    float drho_out;  // rho_out - 1, rounded once from FP64
 };
 
 // Launchers (lbm_kernels.cu).  All enqueue on `stream` and return the launch status.

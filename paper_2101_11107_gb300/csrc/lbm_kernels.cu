@@ -96,12 +96,13 @@ struct Store<LBM_STORE_BF16> {
 // with inward normal n = sign e_axis, in deviation form.  Known: c.n <= 0.  With
 // D = sum_{c.n=0} d + 2 sum_{c.n<0} d (and sum_{c.n=0} w + 2 sum_{c.n<0} w = 1):
 //   inlet:  u.n = U phi, rho = (1 + D)/(1 - u.n);   outlet: rho = rho_out, u.n = 1 - (1 + D)/rho.
+// Both are evaluated as deviations from 1 (rho - 1 = (D + u.n)/(1 - u.n), u.n = (rho_out - 1 - D)/rho_out).
 // The nine unknowns (c.n = +1) by non-equilibrium bounce-back with the full equilibrium; since
 // u has no tangential part, f_eq_i - f_eq_opp(i) = 6 w_i rho u.n.  Then the tangential momentum
 // is zeroed by d_i += c_it D_t / 6, D_t = -sum_j c_jt d_j, which leaves mass and normal
 // momentum unchanged.
 __device__ __forceinline__ void close_open(float (&d)[Q], int kind, int axis, int sgn, float phi,
-                                           float U, float rho_out)
+                                           float U, float rho_out, float drho_out)
 {
     float D = 0.0f;
 #pragma unroll
@@ -115,8 +116,10 @@ __device__ __forceinline__ void close_open(float (&d)[Q], int kind, int axis, in
         un = U * phi;
         rho = 1.0f + (D + un) / (1.0f - un);
     } else {
+        // u.n = 1 - (1 + D)/rho_out written as (drho_out - D)/rho_out, drho_out = rho_out - 1
+        // from the host in FP64, so that D is never rounded against 1
         rho = rho_out;
-        un = 1.0f - (1.0f + D) / rho_out;
+        un = (drho_out - D) / rho_out;
     }
     const float ru6 = 6.0f * rho * un;
 #pragma unroll
@@ -194,7 +197,7 @@ __device__ __forceinline__ void gather(const DomainView& v, const void* __restri
         }
     } else if (kind >= KIND_INLET) {
         const int64_t rec = v.aux[slot];
-        close_open(d, kind, v.io_axis[rec], v.io_sign[rec], v.io_phi[rec], a.U, a.rho_out);
+        close_open(d, kind, v.io_axis[rec], v.io_sign[rec], v.io_phi[rec], a.U, a.rho_out, a.drho_out);
     }
 }
 
