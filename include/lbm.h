@@ -57,6 +57,12 @@ typedef enum {
  *   FP16 / BF16: the scaled deviation (f_i - w_i) / w_i in 16 bits. */
 typedef enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1, LBM_STORE_BF16 = 2 } lbm_storage;
 
+/* Streaming scheme; both give bitwise-identical results.
+ *   AB: pull from one array into a second (two population arrays).
+ *   ESOTERIC: esoteric twist, in place in one array; each cell's update touches only the cells
+ *     x + {0,1}^3 (plus a small side buffer at Bouzidi cells). */
+typedef enum { LBM_SCHEME_AB = 0, LBM_SCHEME_ESOTERIC = 1 } lbm_scheme;
+
 /* Physical parameters (Sec. 2.1.3: S is diagonal in central Hermite moment space). */
 typedef struct {
     double tau;          /* relaxation time of the six second-order moments: rate 1/tau,
@@ -69,6 +75,7 @@ typedef struct {
     double rho_out;      /* density imposed at outlet cells; default 1 */
     int32_t periodic[3]; /* nonzero: the axis wraps (its extent must be a multiple of 4) */
     int32_t storage;     /* lbm_storage */
+    int32_t scheme;      /* lbm_scheme; default ESOTERIC */
 } lbm_params;
 
 /* Device memory callbacks: return a device pointer aligned to 256 bytes, or NULL. */
@@ -88,6 +95,8 @@ typedef struct {
     int32_t bytes_per_value; /* 4 (FP32) or 2 (FP16/BF16) */
     int64_t device_bytes;    /* device memory held by the domain */
     int32_t launch_config;   /* launch configuration of the step kernel in use */
+    int32_t scheme;          /* lbm_scheme */
+    int64_t n_store_bricks;  /* bricks with population storage (active + twist halo) */
 } lbm_info;
 
 typedef struct {
@@ -99,7 +108,8 @@ typedef struct {
     int64_t time;
 } lbm_diagnostics;
 
-/* Fills *p with the defaults: tau 0.6, omega_hi 1, no force, rho_out 1, not periodic, FP32. */
+/* Fills *p with the defaults: tau 0.6, omega_hi 1, no force, rho_out 1, not periodic, FP32,
+ * esoteric twist. */
 void lbm_default_params(lbm_params* p);
 
 /*
@@ -169,11 +179,11 @@ lbm_status lbm_get_diagnostics(lbm_domain* dom, lbm_diagnostics* out);
 lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
 
 /* Number of launch configurations of the fused step kernel. */
-#define LBM_N_LAUNCH_CONFIGS 6
+#define LBM_N_LAUNCH_CONFIGS 4
 
-/* Selects the step kernel's launch configuration: 0..5 = 256 threads (four 4^3 bricks) per CTA
- * with a register budget for 2, 3 or 4 resident CTAs per SM; 128 threads with 6 or 8; 512
- * threads with 1.  Results do not depend on it.  Default 1.  Errors: INVALID_ARG. */
+/* Selects the step kernel's launch configuration: 0, 1 = 256 threads (four 4^3 bricks) per CTA
+ * with a register budget for 3 or 4 resident CTAs per SM; 2, 3 = 128 threads with 6 or 8.
+ * Results do not depend on it.  Default 3.  Errors: INVALID_ARG. */
 lbm_status lbm_set_launch_config(lbm_domain* dom, int32_t config);
 
 /* Times every launch configuration on this domain (trial_steps steps each, CUDA events on the

@@ -1,0 +1,634 @@
+// lbm_device.cuh -- device code of the fused stream-collide step and its companions, templated
+// on the storage precision, the streaming scheme and the launch shape.  Included by one
+// translation unit per storage precision (lbm_step_fp32.cu, lbm_step_fp16.cu, lbm_step_bf16.cu).
+//
+// Method (Hosseini et al.):
+//   LBE f_i(x + c_i, n + 1) = f_i(x, n) + Omega_i             (Sec. 2.1.1, first equation)
+//   Omega = T^-1 S T (f_eq - f), central Hermite moments       (Sec. 2.1.3)
+//   T f_eq = (rho, 0, ..., 0) with the full-expansion f_eq     (Eq. Hermite_coeff_eq)
+//   Bouzidi interpolated bounce-back, q = |x_f - x_s| / |c|    (Sec. 2.1.4)
+//
+// GB300 design:
+//   * Populations are SoA, pop[i][slot], slot = brick * 64 + local cell of a 4x4x4 brick; only
+//     bricks with fluid (and, for the twist, their +{0,1}^3 neighbours) are stored.  One thread
+//     per slot, one CTA per BRICKS bricks; the CTA's brick-neighbour rows are staged in shared
+//     memory, so streaming reads no per-cell neighbour index.
+//   * Two streaming schemes, same arithmetic, bitwise-equal results:
+//       A-B (pull from array A, write to array B): 26 neighbour cells per update;
+//       esoteric twist (in place, one array): the thread of cell x touches only the 8 cells
+//       x + {0,1}^3.  On even levels it reads f_i from slot i of cell x + p_opp(i) and writes
+//       f*_i to slot opp(i) of cell x + p_i; odd levels swap the two slot roles
+//       (p_i = max(c_i, 0)).  Every location is read and then written by one thread only.
+//   * Every lane issues all 27 loads unconditionally; halfway bounce-back is folded into the
+//     address (A-B: the cell's own opposite slot; twist: the swapped slot of the same cell).
+//   * A per-slot 32-bit word carries the wall mask and the cell kind, so bulk cells take no
+//     boundary branch.
+//   * Arithmetic is FP32 on deviations d_i = f_i - w_i throughout (moments, transforms,
+//     relaxation, closures): the O(1) rest-state weights never enter a rounding.
+//   * The 27x27 transform runs as three passes of nine 1-D three-point transforms
+//     (T = M(u_x) (x) M(u_y) (x) M(u_z)), forward and inverse, about 500 FP32 flops per cell.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace dev {
+
+constexpr float CS2 = 1.0f / 3.0f;
+
+// ------------------------------------------------------------------------------ storage
+// FP32 stores d_i; FP16 / BF16 store d_i / w_i.  `load` may use the read-only path (arrays
+// not written by the kernel); `load_rw` is a plain load (the in-place array).
+template <int ST>
+struct Store;
+
+template <>
+struct Store<LBM_STORE_FP32> {
+    using T = float;
+    static __device__ __forceinline__ float load(const void* p, int, uint32_t off)
+    {
+        return __ldg(static_cast<const float*>(p) + off);
+    }
+    static __device__ __forceinline__ float load_rw(const void* p, int, uint32_t off)
+    {
+        return static_cast<const float*>(p)[off];
+    }
+    static __device__ __forceinline__ void store(void* p, int, uint32_t off, float v)
+    {
+        static_cast<float*>(p)[off] = v;
+    }
+};
+
+template <>
+struct Store<LBM_STORE_FP16> {
+    using T = __half;
+    static __device__ __forceinline__ float load(const void* p, int i, uint32_t off)
+    {
+        return w_of(i) * __half2float(__ldg(static_cast<const __half*>(p) + off));
+    }
+    static __device__ __forceinline__ float load_rw(const void* p, int i, uint32_t off)
+    {
+        return w_of(i) * __half2float(static_cast<const __half*>(p)[off]);
+    }
+    static __device__ __forceinline__ void store(void* p, int i, uint32_t off, float v)
+    {
+        static_cast<__half*>(p)[off] = __float2half_rn(v * inv_w_of(i));
+    }
+};
+
+template <>
+struct Store<LBM_STORE_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float load(const void* p, int i, uint32_t off)
+    {
+        return w_of(i) * __bfloat162float(__ldg(static_cast<const __nv_bfloat16*>(p) + off));
+    }
+    static __device__ __forceinline__ float load_rw(const void* p, int i, uint32_t off)
+    {
+        return w_of(i) * __bfloat162float(static_cast<const __nv_bfloat16*>(p)[off]);
+    }
+    static __device__ __forceinline__ void store(void* p, int i, uint32_t off, float v)
+    {
+        static_cast<__nv_bfloat16*>(p)[off] = __float2bfloat16_rn(v * inv_w_of(i));
+    }
+};
+
+// ------------------------------------------------------------------------------ streaming
+// A-B pull: f_i(x, n) = f*_i(x - c_i, n - 1) from `src`; a wall link reads the cell's own
+// opposite slot (halfway bounce-back f_i(x, n) = f*_opp(i)(x, n - 1)).
+template <int ST>
+__device__ __forceinline__ void fetch_ab(const void* __restrict__ src, uint32_t n, const int32_t* nbrow,
+                                         uint32_t slot, uint32_t wm, float (&d)[Q])
+{
+    const int l = (int)(slot & (BRICK_CELLS - 1));
+    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
+        // sx in [-1, 4]: the arithmetic shift gives the brick offset -1, 0 or +1
+        const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+        const uint32_t nb = (uint32_t)nbrow[ob];
+        const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
+        const bool wall = (wm >> i) & 1u;
+        const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
+        d[i] = Store<ST>::load(src, i, off);
+    }
+}
+
+// Slots of the 8 cells x + e, e in {0,1}^3 (index ex + 2 ey + 4 ez), from the brick's nb8 row.
+__device__ __forceinline__ void corner_slots(const int32_t* nb8, uint32_t slot, uint32_t (&cs)[8])
+{
+    const int l = (int)(slot & (BRICK_CELLS - 1));
+    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int tx = lx + (e & 1), ty = ly + ((e >> 1) & 1), tz = lz + (e >> 2);
+        const int ob = (tx >> 2) | ((ty >> 2) << 1) | ((tz >> 2) << 2);
+        cs[e] = (uint32_t)nb8[ob] * BRICK_CELLS + (uint32_t)((tx & 3) + ((ty & 3) << 2) + ((tz & 3) << 4));
+    }
+}
+
+// Esoteric twist read at level parity P: f_i from slot (P ? opp(i) : i) of cell x + p_opp(i);
+// on a wall link the other slot of the same cell, which holds f*_opp(i)(x, n - 1).
+template <int ST, bool RW>
+__device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint32_t (&cs)[8], uint32_t wm,
+                                         int parity, float (&d)[Q])
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint32_t flip = ((uint32_t)parity ^ (wm >> i)) & 1u;
+        const uint32_t dir = flip ? (uint32_t)(Q - 1 - i) : (uint32_t)i;
+        const uint32_t off = dir * n + cs[corner_neg(i)];
+        d[i] = RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off);
+    }
+}
+
+// Esoteric twist write after a step of parity P: f*_i to slot (P ? i : opp(i)) of cell x + p_i.
+template <int ST>
+__device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (&cs)[8], int parity,
+                                         const float (&d)[Q])
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint32_t dir = parity ? (uint32_t)i : (uint32_t)(Q - 1 - i);
+        Store<ST>::store(pop, i, dir * n + cs[corner_pos(i)], d[i]);
+    }
+}
+
+// ------------------------------------------------------------------------------ boundaries
+// Open-boundary closure of an inlet (velocity) or outlet (density) cell on an axis-aligned face
+// with inward normal n = sign e_axis, in deviation form.  Known: c.n <= 0.  With
+// D = sum_{c.n=0} d + 2 sum_{c.n<0} d (and sum_{c.n=0} w + 2 sum_{c.n<0} w = 1):
+//   inlet:  u.n = U phi, rho = (1 + D)/(1 - u.n);   outlet: rho = rho_out, u.n = 1 - (1 + D)/rho.
+// Both are evaluated as deviations from 1 (rho - 1 = (D + u.n)/(1 - u.n),
+// u.n = (rho_out - 1 - D)/rho_out), so that D is never rounded against 1.
+// The nine unknowns (c.n = +1) by non-equilibrium bounce-back with the full equilibrium; since
+// u has no tangential part, f_eq_i - f_eq_opp(i) = 6 w_i rho u.n.  Then the tangential momentum
+// is zeroed by d_i += c_it D_t / 6, D_t = -sum_j c_jt d_j, which leaves mass and normal
+// momentum unchanged.
+__device__ __forceinline__ void close_open(float (&d)[Q], int kind, int axis, int sgn, float phi, float U,
+                                           float rho_out, float drho_out)
+{
+    float D = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cn = sgn * (axis == 0 ? cx_of(i) : axis == 1 ? cy_of(i) : cz_of(i));
+        if (cn == 0) D += d[i];
+        if (cn < 0) D += 2.0f * d[i];
+    }
+    float rho, un;
+    if (kind == KIND_INLET) {
+        un = U * phi;
+        rho = 1.0f + (D + un) / (1.0f - un);
+    } else {
+        rho = rho_out;
+        un = (drho_out - D) / rho_out;
+    }
+    const float ru6 = 6.0f * rho * un;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cn = sgn * (axis == 0 ? cx_of(i) : axis == 1 ? cy_of(i) : cz_of(i));
+        if (cn == 1) d[i] = d[Q - 1 - i] + w_of(i) * ru6;
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        if (t == axis) continue;
+        float mom = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int ct = t == 0 ? cx_of(j) : t == 1 ? cy_of(j) : cz_of(j);
+            if (ct == 1) mom += d[j];
+            if (ct == -1) mom -= d[j];
+        }
+        const float corr = -mom * (1.0f / 6.0f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cn = sgn * (axis == 0 ? cx_of(i) : axis == 1 ? cy_of(i) : cz_of(i));
+            const int ct = t == 0 ? cx_of(i) : t == 1 ? cy_of(i) : cz_of(i);
+            if (cn == 1 && ct != 0) d[i] += ct == 1 ? corr : -corr;
+        }
+    }
+}
+
+// Wall rules on top of the bounce-back already in d (Sec. 2.1.4 in pull form, beta = opp(alpha)
+// pointing into the wall):
+//   q <  1/2: f_a(x) = 2q f*_b(x) + (1 - 2q) f*_b(x + c_a)  [= the value pulled for b]
+//   q >= 1/2: f_a(x) = f*_b(x)/(2q) + (2q - 1)/(2q) f*_a(x)
+// with halfway bounce-back kept if x + c_a is not fluid in the first branch; then the open
+// boundaries.  f*_a(x, n - 1) comes from the cell's own slot (A-B) or from the side buffer
+// (twist: that slot is the one x + c_a pulls and overwrites in this step).  Returns the mask of
+// the q >= 1/2 links, whose f*_a the twist must keep in the side buffer.
+template <int ST, int SCHEME>
+__device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* src_ab, uint32_t slot,
+                                               uint32_t word, const LevelArgs& a, float (&d)[Q])
+{
+    const uint32_t wm = word & WORD_WALL_MASK;
+    const int kind = (int)((word >> WORD_KIND_SHIFT) & 3u);
+    uint32_t half = 0u;
+    if (kind == KIND_BOUZIDI) {
+        const uint32_t rec = (uint32_t)v.aux[slot];
+        const uint32_t nbq = (uint32_t)v.n_bq;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (!(wm & (1u << i))) continue;
+            const float q = __ldg(v.bq + (uint32_t)i * nbq + rec);
+            if (q > 0.0f) {
+                if (q < 0.5f) {
+                    if (!(wm & (1u << (Q - 1 - i)))) d[i] = 2.0f * q * d[i] + (1.0f - 2.0f * q) * d[Q - 1 - i];
+                } else {
+                    const float inv2q = 0.5f / q;
+                    const float fa = (SCHEME == LBM_SCHEME_ESOTERIC)
+                                         ? Store<ST>::load_rw(v.side, i, (uint32_t)i * nbq + rec)
+                                         : Store<ST>::load(src_ab, i, (uint32_t)i * (uint32_t)v.n_slots + slot);
+                    d[i] = inv2q * d[i] + (1.0f - inv2q) * fa;
+                    half |= 1u << i;
+                }
+            }
+        }
+    } else if (kind >= KIND_INLET) {
+        const int64_t rec = v.aux[slot];
+        close_open(d, kind, v.io_axis[rec], v.io_sign[rec], v.io_phi[rec], a.U, a.rho_out, a.drho_out);
+    }
+    return half;
+}
+
+// ------------------------------------------------------------------------------ collide
+__device__ __forceinline__ void fwd3(float& gm, float& g0, float& gp, float u, float u2mcs)
+{
+    // (g(-1), g(0), g(+1)) -> central Hermite moments (m0, m1, m2) about u
+    const float m0 = gm + g0 + gp;
+    const float s1 = gp - gm;
+    const float s2 = gp + gm;
+    gm = m0;
+    g0 = fmaf(-u, m0, s1);
+    gp = fmaf(u2mcs, m0, fmaf(-2.0f * u, s1, s2));
+}
+
+__device__ __forceinline__ void inv3(float& m0, float& m1, float& m2, float u, float u2pcs)
+{
+    // (m0, m1, m2) -> (g(-1), g(0), g(+1)): raw sums S1 = g+ - g-, S2 = g+ + g-
+    const float S1 = fmaf(u, m0, m1);
+    const float S2 = fmaf(u2pcs, m0, fmaf(2.0f * u, m1, m2));
+    const float g0 = m0 - S2;
+    m0 = 0.5f * (S2 - S1);
+    m2 = 0.5f * (S2 + S1);
+    m1 = g0;
+}
+
+__host__ __device__ constexpr int order_of(int m) { return m % 3 + (m / 3) % 3 + m / 9; }
+
+struct Moments {
+    float rho, ux, uy, uz;
+};
+
+__device__ __forceinline__ Moments moments(const float (&d)[Q], const float g[3])
+{
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += d[i];
+        if (cx_of(i) == 1) jx += d[i];
+        if (cx_of(i) == -1) jx -= d[i];
+        if (cy_of(i) == 1) jy += d[i];
+        if (cy_of(i) == -1) jy -= d[i];
+        if (cz_of(i) == 1) jz += d[i];
+        if (cz_of(i) == -1) jz -= d[i];
+    }
+    Moments m;
+    m.rho = 1.0f + drho;
+    const float ir = 1.0f / m.rho;
+    m.ux = fmaf(jx, ir, 0.5f * g[0]);
+    m.uy = fmaf(jy, ir, 0.5f * g[1]);
+    m.uz = fmaf(jz, ir, 0.5f * g[2]);
+    return m;
+}
+
+// CHM-MRT collision in deviation form.  With a = T(u) f, a_w = T(u) w (per axis (1, -u, u^2))
+// and the post-collision moments a* (a*_0 = rho, first order rho g / 2 from the half-force
+// forcing, a*_m = (1 - s_m) a_m for order >= 2 since a_eq = 0 there), the outgoing deviation
+// is d* = T^-1(u) (a* - a_w), with a - a_w = T(u) d.
+__device__ __forceinline__ void collide(float (&d)[Q], const LevelArgs& a)
+{
+    const Moments M = moments(d, a.g);
+    const float ux = M.ux, uy = M.uy, uz = M.uz;
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    // forward T(u) d: passes along x, y, z
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fwd3(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, ux2 - CS2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) fwd3(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, uy2 - CS2);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) fwd3(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, uz2 - CS2);
+    // relaxation: b = a* - a_w
+    const float ex[3] = {1.0f, -ux, ux2}, ey[3] = {1.0f, -uy, uy2}, ez[3] = {1.0f, -uz, uz2};
+    const float s[7] = {0.0f, 0.0f, a.s2, a.s3, a.s4, a.s5, a.s6};
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        const int o = order_of(m);
+        if (o == 1) {
+            const float gk = (m == 1) ? a.g[0] : (m == 3) ? a.g[1] : a.g[2];
+            const float uk = (m == 1) ? ux : (m == 3) ? uy : uz;
+            d[m] = fmaf(0.5f * M.rho, gk, uk);
+        } else if (o >= 2) {
+            const float aw = ex[m % 3] * ey[(m / 3) % 3] * ez[m / 9];
+            d[m] = (1.0f - s[o]) * d[m] - s[o] * aw;
+        }
+    }
+    // inverse T(u)^-1
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) inv3(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, uz2 + CS2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) inv3(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, uy2 + CS2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) inv3(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, ux2 + CS2);
+}
+
+// ------------------------------------------------------------------------------ gather (read-only)
+// Populations of level n of one fluid cell, for the export and diagnostics kernels.
+template <int ST, int SCHEME>
+__device__ __forceinline__ void gather(const DomainView& v, const void* src, uint32_t slot, uint32_t word,
+                                       const LevelArgs& a, float (&d)[Q])
+{
+    const uint32_t wm = word & WORD_WALL_MASK;
+    const uint32_t n = (uint32_t)v.n_slots;
+    if (SCHEME == LBM_SCHEME_ESOTERIC) {
+        uint32_t cs[8];
+        corner_slots(v.nb8 + (slot / BRICK_CELLS) * 8, slot, cs);
+        fetch_et<ST, false>(src, n, cs, wm, a.parity, d);
+    } else {
+        fetch_ab<ST>(src, n, v.nbr + (slot / BRICK_CELLS) * Q, slot, wm, d);
+    }
+    if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
+}
+
+// ------------------------------------------------------------------------------ kernels
+template <int ST, int SCHEME, int BRICKS, int MINB>
+__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
+    k_step(DomainView v, const void* src, void* dst, LevelArgs a)
+{
+    constexpr int NB = (SCHEME == LBM_SCHEME_ESOTERIC) ? 8 : Q;
+    __shared__ int32_t s_nb[BRICKS * NB];
+    const int32_t* table = (SCHEME == LBM_SCHEME_ESOTERIC) ? v.nb8 : v.nbr;
+    const int64_t brick0 = (int64_t)blockIdx.x * BRICKS;
+    for (int t = threadIdx.x; t < BRICKS * NB; t += blockDim.x)
+        s_nb[t] = (brick0 + t / NB < v.n_bricks) ? __ldg(table + brick0 * NB + t) : -1;
+    __syncthreads();
+    const uint32_t slot = (uint32_t)(brick0 * BRICK_CELLS) + threadIdx.x;
+    if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
+    const uint32_t word = __ldg(v.word + slot);
+    if (!(word & WORD_FLUID)) return;
+    const uint32_t wm = word & WORD_WALL_MASK;
+    const uint32_t n = (uint32_t)v.n_slots;
+    const int32_t* row = s_nb + (threadIdx.x / BRICK_CELLS) * NB;
+    float d[Q];
+    if (SCHEME == LBM_SCHEME_ESOTERIC) {
+        uint32_t cs[8];
+        corner_slots(row, slot, cs);
+        fetch_et<ST, true>(dst, n, cs, wm, a.parity, d);
+        const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
+        collide(d, a);
+        store_et<ST>(dst, n, cs, a.parity, d);
+        if (half) {
+            const uint32_t rec = (uint32_t)v.aux[slot];
+            const uint32_t nbq = (uint32_t)v.n_bq;
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (half & (1u << i)) Store<ST>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
+        }
+    } else {
+        fetch_ab<ST>(src, n, row, slot, wm, d);
+        if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
+        collide(d, a);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
+    }
+}
+
+template <int ST, int SCHEME>
+__global__ void __launch_bounds__(256)
+    k_macroscopic(DomainView v, const void* src, LevelArgs a, const int32_t* fl_slot, const int32_t* fl_box,
+                  int64_t n_fluid, int dense, float* rho, float* u, int64_t n_out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_fluid) return;
+    const uint32_t slot = (uint32_t)fl_slot[k];
+    float d[Q];
+    gather<ST, SCHEME>(v, src, slot, v.word[slot], a, d);
+    const Moments M = moments(d, a.g);
+    const int64_t o = dense ? (int64_t)fl_box[k] : k;
+    rho[o] = M.rho;
+    u[o] = M.ux;
+    u[n_out + o] = M.uy;
+    u[2 * n_out + o] = M.uz;
+}
+
+// Post-collision populations of the previous level := f_eq(rho, u) (full expansion, product
+// form), written as deviations d_i = rho (prod psi - w_i) + (rho - 1) w_i with
+// prod psi - w = dpx psi_y psi_z + w1x dpy psi_z + w1x w1y dpz, dpsi(0) = -u^2,
+// dpsi(+-1) = (+-u + u^2)/2.  A-B: into the cell's own slots; twist: where the step of parity
+// `parity_prev` would have written them, plus every direction into the side buffer of a
+// Bouzidi cell.
+template <int ST, int SCHEME>
+__global__ void __launch_bounds__(256)
+    k_init_equilibrium(DomainView v, void* dst, int parity_prev, const int32_t* fl_slot, const int32_t* fl_box,
+                       int64_t n_fluid, const float* rho_in, const float* u_in, int64_t n_box)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_fluid) return;
+    const int64_t b = fl_box[k];
+    const uint32_t slot = (uint32_t)fl_slot[k];
+    const float rho = rho_in[b];
+    const float u[3] = {u_in[b], u_in[n_box + b], u_in[2 * n_box + b]};
+    float dp[3][3], ps[3][3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float uu = u[ax] * u[ax];
+        dp[ax][0] = 0.5f * (uu - u[ax]);
+        dp[ax][1] = -uu;
+        dp[ax][2] = 0.5f * (uu + u[ax]);
+        ps[ax][0] = 1.0f / 6.0f + dp[ax][0];
+        ps[ax][1] = 2.0f / 3.0f + dp[ax][1];
+        ps[ax][2] = 1.0f / 6.0f + dp[ax][2];
+    }
+    float d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int ix = cx_of(i) + 1, iy = cy_of(i) + 1, iz = cz_of(i) + 1;
+        const float w1x = w1_of(cx_of(i)), w1y = w1_of(cy_of(i));
+        const float dprod = dp[0][ix] * ps[1][iy] * ps[2][iz] + w1x * dp[1][iy] * ps[2][iz] + w1x * w1y * dp[2][iz];
+        d[i] = fmaf(rho, dprod, (rho - 1.0f) * w_of(i));
+    }
+    const uint32_t n = (uint32_t)v.n_slots;
+    if (SCHEME == LBM_SCHEME_ESOTERIC) {
+        uint32_t cs[8];
+        corner_slots(v.nb8 + (slot / BRICK_CELLS) * 8, slot, cs);
+        store_et<ST>(dst, n, cs, parity_prev, d);
+        const uint32_t word = v.word[slot];
+        if (((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) {
+            const uint32_t rec = (uint32_t)v.aux[slot];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Store<ST>::store(v.side, i, (uint32_t)i * (uint32_t)v.n_bq + rec, d[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
+    }
+}
+
+// FP64 diagnostics: per-block partial sums in a fixed order; one block then reduces the
+// partials in a fixed order (reproducible run to run).
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_FIELDS = 5;  // mass, flux_in, flux_out, max|u|, non-finite count
+
+__device__ __forceinline__ void block_reduce5(double (&x)[DIAG_FIELDS], double* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int f = 0; f < DIAG_FIELDS; ++f) {
+            const double o = __shfl_down_sync(0xffffffffu, x[f], off);
+            x[f] = (f == 3) ? fmax(x[f], o) : x[f] + o;
+        }
+    }
+    if (lane == 0)
+        for (int f = 0; f < DIAG_FIELDS; ++f) sh[warp * DIAG_FIELDS + f] = x[f];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < DIAG_THREADS / 32; ++w)
+            for (int f = 0; f < DIAG_FIELDS; ++f)
+                x[f] = (f == 3) ? fmax(x[f], sh[w * DIAG_FIELDS + f]) : x[f] + sh[w * DIAG_FIELDS + f];
+    }
+}
+
+template <int ST, int SCHEME>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_diagnostics(DomainView v, const void* src, LevelArgs a, const int32_t* fl_slot, int64_t n_fluid,
+                  double* partials)
+{
+    __shared__ double sh[(DIAG_THREADS / 32) * DIAG_FIELDS];
+    double x[DIAG_FIELDS] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const int64_t k = (int64_t)blockIdx.x * DIAG_THREADS + threadIdx.x;
+    if (k < n_fluid) {
+        const uint32_t slot = (uint32_t)fl_slot[k];
+        const uint32_t word = v.word[slot];
+        float d[Q];
+        gather<ST, SCHEME>(v, src, slot, word, a, d);
+        const Moments M = moments(d, a.g);
+        const bool finite = isfinite(M.rho) && isfinite(M.ux) && isfinite(M.uy) && isfinite(M.uz);
+        if (finite) {
+            x[0] = (double)M.rho;
+            const int kind = (int)((word >> WORD_KIND_SHIFT) & 3u);
+            if (kind >= KIND_INLET) {
+                const int64_t rec = v.aux[slot];
+                const int ax = v.io_axis[rec];
+                const float un = v.io_sign[rec] * (ax == 0 ? M.ux : ax == 1 ? M.uy : M.uz);
+                if (kind == KIND_INLET) x[1] = (double)M.rho * (double)un;
+                else x[2] = -(double)M.rho * (double)un;
+            }
+            x[3] = sqrt((double)M.ux * M.ux + (double)M.uy * M.uy + (double)M.uz * M.uz);
+        } else {
+            x[4] = 1.0;
+        }
+    }
+    block_reduce5(x, sh);
+    if (threadIdx.x == 0)
+        for (int f = 0; f < DIAG_FIELDS; ++f) partials[(int64_t)blockIdx.x * DIAG_FIELDS + f] = x[f];
+}
+
+inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// ------------------------------------------------------------------------------ launchers
+// Launch configurations of the step kernel: (bricks per CTA, minimum resident CTAs per SM);
+// the second number sets the register budget, 65536 / (threads * CTAs).
+template <int ST, int SCHEME, int BRICKS, int MINB>
+cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const LevelArgs& a, cudaStream_t s)
+{
+    if (v.n_bricks == 0) return cudaSuccess;
+    k_step<ST, SCHEME, BRICKS, MINB><<<grid_for(v.n_bricks, BRICKS), BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+    return cudaGetLastError();
+}
+
+template <int ST, int SCHEME>
+cudaError_t launch_step_scheme(int config, const DomainView& v, const void* src, void* dst, const LevelArgs& a,
+                               cudaStream_t s)
+{
+    switch (config) {
+    case 0: return launch_step_t<ST, SCHEME, 4, 3>(v, src, dst, a, s);
+    case 1: return launch_step_t<ST, SCHEME, 4, 4>(v, src, dst, a, s);
+    case 2: return launch_step_t<ST, SCHEME, 2, 6>(v, src, dst, a, s);
+    default: return launch_step_t<ST, SCHEME, 2, 8>(v, src, dst, a, s);
+    }
+}
+
+template <int ST>
+cudaError_t launch_step(int scheme, int config, const DomainView& v, const void* src, void* dst,
+                        const LevelArgs& a, cudaStream_t s)
+{
+    return scheme == LBM_SCHEME_ESOTERIC ? launch_step_scheme<ST, LBM_SCHEME_ESOTERIC>(config, v, src, dst, a, s)
+                                         : launch_step_scheme<ST, LBM_SCHEME_AB>(config, v, src, dst, a, s);
+}
+
+template <int ST>
+cudaError_t launch_macroscopic(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid, int dense, float* rho,
+                               float* u, int64_t n_out, cudaStream_t s)
+{
+    if (n_fluid == 0) return cudaSuccess;
+    if (scheme == LBM_SCHEME_ESOTERIC)
+        k_macroscopic<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, src, a, fl_slot, fl_box,
+                                                                                  n_fluid, dense, rho, u, n_out);
+    else
+        k_macroscopic<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, src, a, fl_slot, fl_box, n_fluid,
+                                                                            dense, rho, u, n_out);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_init_equilibrium(int scheme, const DomainView& v, void* dst, int parity_prev,
+                                    const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,
+                                    const float* rho, const float* u, int64_t n_box, cudaStream_t s)
+{
+    if (n_fluid == 0) return cudaSuccess;
+    if (scheme == LBM_SCHEME_ESOTERIC)
+        k_init_equilibrium<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, 256), 256, 0, s>>>(
+            v, dst, parity_prev, fl_slot, fl_box, n_fluid, rho, u, n_box);
+    else
+        k_init_equilibrium<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, 256), 256, 0, s>>>(
+            v, dst, parity_prev, fl_slot, fl_box, n_fluid, rho, u, n_box);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_diagnostics(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, int64_t n_fluid, double* partials, cudaStream_t s)
+{
+    const int nb = (int)diagnostics_blocks(n_fluid);
+    if (scheme == LBM_SCHEME_ESOTERIC)
+        k_diagnostics<ST, LBM_SCHEME_ESOTERIC><<<nb, DIAG_THREADS, 0, s>>>(v, src, a, fl_slot, n_fluid, partials);
+    else
+        k_diagnostics<ST, LBM_SCHEME_AB><<<nb, DIAG_THREADS, 0, s>>>(v, src, a, fl_slot, n_fluid, partials);
+    return cudaGetLastError();
+}
+
+template <int ST>
+const Launchers& make_launchers()
+{
+    static const Launchers L = {&launch_step<ST>, &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
+                                &launch_diagnostics<ST>};
+    return L;
+}
+
+}  // namespace dev
+}  // namespace lbm

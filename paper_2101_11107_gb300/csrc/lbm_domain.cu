@@ -34,12 +34,15 @@ lbm_status cuda_fail(cudaError_t e, const char* where)
 struct lbm_domain {
     int32_t nx = 0, ny = 0, nz = 0;
     lbm_params params{};
-    int64_t n_fluid = 0, n_bricks = 0, n_slots = 0, n_bq = 0, n_io = 0, n_wall = 0;
+    int64_t n_fluid = 0, n_bricks = 0, n_store_bricks = 0, n_slots = 0, n_bq = 0, n_io = 0, n_wall = 0;
     DomainView view{};
     int32_t* d_fl_slot = nullptr;
     int32_t* d_fl_box = nullptr;
     void* d_pop[2] = {nullptr, nullptr};
-    int cur = 0;  // d_pop[cur] holds the post-collision populations of level time - 1
+    // A-B: d_pop[cur] holds the post-collision populations of level time - 1; esoteric twist:
+    // d_pop[0] holds them in place, arranged for a read of parity time & 1
+    int cur = 0;
+    void* d_side = nullptr;  // twist: f* of q >= 1/2 Bouzidi links, [27][n_bq]
     int launch_config = DEFAULT_LAUNCH_CONFIG;
     double* d_partials = nullptr;
     lbm_diagnostics* d_diag = nullptr;
@@ -60,6 +63,10 @@ struct lbm_domain {
 
     int bytes_per_value() const { return params.storage == LBM_STORE_FP32 ? 4 : 2; }
     size_t pop_bytes() const { return (size_t)Q * (size_t)n_slots * (size_t)bytes_per_value(); }
+    size_t side_bytes() const { return (size_t)Q * (size_t)std::max<int64_t>(n_bq, 1) * (size_t)bytes_per_value(); }
+    bool twist() const { return params.scheme == LBM_SCHEME_ESOTERIC; }
+    void* src() const { return d_pop[twist() ? 0 : cur]; }
+    void* dst() const { return d_pop[twist() ? 0 : 1 - cur]; }
 
     void* dev_alloc(size_t bytes)
     {
@@ -113,6 +120,7 @@ struct lbm_domain {
         a.s6 = (float)params.omega_hi[3];
         a.rho_out = (float)params.rho_out;
         a.drho_out = (float)(params.rho_out - 1.0);
+        a.parity = (int)(n & 1);
         return a;
     }
 };
@@ -149,6 +157,7 @@ lbm_status check_params(const lbm_params& p)
             return fail(LBM_ERR_INVALID_ARG, "omega_hi must lie in (0, 2)");
     if (!(p.rho_out > 0.0) || !std::isfinite(p.rho_out)) return fail(LBM_ERR_INVALID_ARG, "rho_out must be > 0");
     if (p.storage < LBM_STORE_FP32 || p.storage > LBM_STORE_BF16) return fail(LBM_ERR_INVALID_ARG, "bad storage");
+    if (p.scheme != LBM_SCHEME_AB && p.scheme != LBM_SCHEME_ESOTERIC) return fail(LBM_ERR_INVALID_ARG, "bad scheme");
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p.force[d]) || !std::isfinite(p.force_amp[d]))
             return fail(LBM_ERR_INVALID_ARG, "non-finite force");
@@ -168,6 +177,7 @@ void lbm_default_params(lbm_params* p)
     for (int k = 0; k < 4; ++k) p->omega_hi[k] = 1.0;
     p->rho_out = 1.0;
     p->storage = LBM_STORE_FP32;
+    p->scheme = LBM_SCHEME_ESOTERIC;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -214,32 +224,61 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
             for (int x = 0; x < nx; ++x)
                 if (mask[x + (int64_t)nx * (y + (int64_t)ny * z)])
                     brick_id[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nby * (z >> 2))] = 0;
+    // active bricks (holding fluid) are numbered first, in box order; then, for the esoteric
+    // twist, every brick at an offset in {0,1}^3 of an active one (storage for the links of the
+    // update's 8-cell corner), on a brick grid extended by one along non-periodic axes
+    const int nb3[3] = {nbx, nby, nbz};
+    int eb3[3];
+    for (int d = 0; d < 3; ++d) eb3[d] = nb3[d] + (P.periodic[d] ? 0 : 1);
+    const int64_t n_ext = (int64_t)eb3[0] * eb3[1] * eb3[2];
+    std::vector<int32_t> store_id((size_t)n_ext, -1);
+    auto ext_index = [&](int bx, int by, int bz) -> int64_t { return bx + (int64_t)eb3[0] * (by + (int64_t)eb3[1] * bz); };
     int64_t n_bricks = 0;
-    std::vector<int32_t> brick_pos;  // (bx, by, bz) per brick
+    std::vector<int32_t> brick_pos;  // (bx, by, bz) per active brick
     for (int64_t bb = 0; bb < n_brick_box; ++bb)
         if (brick_id[bb] == 0) {
-            brick_id[bb] = (int32_t)n_bricks++;
-            brick_pos.push_back((int32_t)(bb % nbx));
-            brick_pos.push_back((int32_t)((bb / nbx) % nby));
-            brick_pos.push_back((int32_t)(bb / ((int64_t)nbx * nby)));
+            const int bx = (int)(bb % nbx), by = (int)((bb / nbx) % nby), bz = (int)(bb / ((int64_t)nbx * nby));
+            brick_id[bb] = (int32_t)n_bricks;
+            store_id[(size_t)ext_index(bx, by, bz)] = (int32_t)n_bricks++;
+            brick_pos.push_back(bx);
+            brick_pos.push_back(by);
+            brick_pos.push_back(bz);
         }
-    const int64_t n_slots = n_bricks * BRICK_CELLS;
+    // brick at offset o of brick b along each axis, wrapped on periodic axes; -1 off the grid
+    auto offset_brick = [&](int64_t b, int ox, int oy, int oz, bool extended) -> int64_t {
+        int p[3] = {brick_pos[3 * b] + ox, brick_pos[3 * b + 1] + oy, brick_pos[3 * b + 2] + oz};
+        for (int d = 0; d < 3; ++d) {
+            const int lim = extended ? eb3[d] : nb3[d];
+            if (p[d] < 0 || p[d] >= lim) {
+                if (!P.periodic[d]) return -1;
+                p[d] = (p[d] + nb3[d]) % nb3[d];
+            }
+        }
+        return ext_index(p[0], p[1], p[2]);
+    };
+    int64_t n_store = n_bricks;
+    const bool twist = P.scheme == LBM_SCHEME_ESOTERIC;
+    std::vector<int32_t> nb8;
+    if (twist) {
+        nb8.assign((size_t)n_bricks * 8, -1);
+        for (int64_t b = 0; b < n_bricks; ++b)
+            for (int e = 0; e < 8; ++e) {
+                const int64_t x = offset_brick(b, e & 1, (e >> 1) & 1, e >> 2, true);
+                if (store_id[(size_t)x] < 0) store_id[(size_t)x] = (int32_t)n_store++;
+                nb8[(size_t)b * 8 + e] = store_id[(size_t)x];
+            }
+    }
+    const int64_t n_slots = n_store * BRICK_CELLS;
     // kernels address populations with 32-bit element offsets i * n_slots + slot
     if (n_slots * Q >= ((int64_t)1 << 32)) return fail(LBM_ERR_INVALID_ARG, "domain too large (27 x slots >= 2^32)");
-    const int nb3[3] = {nbx, nby, nbz};
-    std::vector<int32_t> nbr((size_t)n_bricks * Q, -1);
-    for (int64_t b = 0; b < n_bricks; ++b) {
-        for (int o = 0; o < Q; ++o) {
-            int p[3] = {brick_pos[3 * b] + cx_of(o), brick_pos[3 * b + 1] + cy_of(o), brick_pos[3 * b + 2] + cz_of(o)};
-            bool ok = true;
-            for (int d = 0; d < 3; ++d) {
-                if (p[d] < 0 || p[d] >= nb3[d]) {
-                    if (P.periodic[d]) p[d] = (p[d] + nb3[d]) % nb3[d];
-                    else ok = false;
-                }
+    std::vector<int32_t> nbr;
+    if (!twist) {
+        nbr.assign((size_t)n_bricks * Q, -1);
+        for (int64_t b = 0; b < n_bricks; ++b)
+            for (int o = 0; o < Q; ++o) {
+                const int64_t x = offset_brick(b, cx_of(o), cy_of(o), cz_of(o), false);
+                if (x >= 0) nbr[(size_t)b * Q + o] = store_id[(size_t)x];
             }
-            if (ok) nbr[(size_t)b * Q + o] = brick_id[p[0] + (int64_t)nbx * (p[1] + (int64_t)nby * p[2])];
-        }
     }
     auto slot_of = [&](int x, int y, int z) -> int64_t {
         const int64_t b = brick_id[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nby * (z >> 2))];
@@ -259,8 +298,9 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     };
 
     // ---------------------------------------------------------------- cell words
-    std::vector<uint32_t> word((size_t)n_slots, 0u);
-    std::vector<int32_t> aux((size_t)n_slots, -1);
+    const int64_t n_active_slots = n_bricks * BRICK_CELLS;
+    std::vector<uint32_t> word((size_t)n_active_slots, 0u);
+    std::vector<int32_t> aux((size_t)n_active_slots, -1);
     std::vector<int32_t> fl_slot, fl_box;
     fl_slot.reserve((size_t)n_fluid);
     fl_box.reserve((size_t)n_fluid);
@@ -364,6 +404,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     D->params = P;
     D->n_fluid = n_fluid;
     D->n_bricks = n_bricks;
+    D->n_store_bricks = n_store;
     D->n_slots = n_slots;
     D->n_bq = n_bq;
     D->n_io = (int64_t)io_phi.size();
@@ -380,6 +421,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
 
     lbm_status st = LBM_OK;
     int32_t* d_nbr = nullptr;
+    int32_t* d_nb8 = nullptr;
     uint32_t* d_word = nullptr;
     int32_t* d_aux = nullptr;
     float* d_bq = nullptr;
@@ -387,6 +429,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     int8_t* d_io_axis = nullptr;
     int8_t* d_io_sign = nullptr;
     if (!st) st = upload(D, &d_nbr, nbr, "brick neighbours");
+    if (!st) st = upload(D, &d_nb8, nb8, "brick corner neighbours");
     if (!st) st = upload(D, &d_word, word, "cell words");
     if (!st) st = upload(D, &d_aux, aux, "aux index");
     if (!st) st = upload(D, &d_bq, bq, "Bouzidi q");
@@ -395,12 +438,20 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     if (!st) st = upload(D, &d_io_sign, io_sign, "open-boundary sign");
     if (!st) st = upload(D, &D->d_fl_slot, fl_slot, "fluid slots");
     if (!st) st = upload(D, &D->d_fl_box, fl_box, "fluid box indices");
-    for (int k = 0; k < 2 && !st; ++k) {
+    for (int k = 0; k < (twist ? 1 : 2) && !st; ++k) {
         D->d_pop[k] = D->dev_alloc(D->pop_bytes());
         if (!D->d_pop[k]) st = fail(LBM_ERR_OOM, "allocation failed: populations");
         else {
             cudaError_t e = cudaMemsetAsync(D->d_pop[k], 0, D->pop_bytes(), D->stream);
             if (e != cudaSuccess) st = cuda_fail(e, "clearing populations");
+        }
+    }
+    if (!st && twist) {
+        D->d_side = D->dev_alloc(D->side_bytes());
+        if (!D->d_side) st = fail(LBM_ERR_OOM, "allocation failed: Bouzidi side buffer");
+        else {
+            cudaError_t e = cudaMemsetAsync(D->d_side, 0, D->side_bytes(), D->stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "clearing the side buffer");
         }
     }
     if (!st) {
@@ -422,6 +473,8 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     v.n_slots = n_slots;
     v.n_bricks = n_bricks;
     v.nbr = d_nbr;
+    v.nb8 = d_nb8;
+    v.side = D->d_side;
     v.word = d_word;
     v.aux = d_aux;
     v.bq = d_bq;
@@ -487,8 +540,11 @@ lbm_status lbm_init_equilibrium(lbm_domain* D, const float* rho, const float* u,
         dr = stage;
         du = stage + n_box;
     }
-    cudaError_t e = launch_init_equilibrium(D->params.storage, D->n_slots, D->d_pop[D->cur], D->d_fl_slot,
-                                            D->d_fl_box, D->n_fluid, dr, du, n_box, D->stream);
+    // the previous level's parity decides where the twist keeps each population
+    const int parity_prev = (int)((D->time + 1) & 1);
+    cudaError_t e = launchers(D->params.storage)
+                        .init_equilibrium(D->params.scheme, D->view, D->src(), parity_prev, D->d_fl_slot, D->d_fl_box,
+                                          D->n_fluid, dr, du, n_box, D->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     if (stage) {
         e = cudaStreamSynchronize(D->stream);
@@ -505,10 +561,10 @@ lbm_status lbm_step(lbm_domain* D, int64_t n)
     if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
     for (int64_t k = 0; k < n; ++k) {
         const LevelArgs a = D->level_args(D->time);
-        cudaError_t e = launch_step(D->params.storage, D->launch_config, D->view, D->d_pop[D->cur],
-                                    D->d_pop[1 - D->cur], a, D->stream);
+        cudaError_t e = launchers(D->params.storage)
+                            .step(D->params.scheme, D->launch_config, D->view, D->src(), D->dst(), a, D->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
-        D->cur = 1 - D->cur;
+        if (!D->twist()) D->cur = 1 - D->cur;
         D->time += 1;
     }
     return LBM_OK;
@@ -531,25 +587,31 @@ lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config
         if (best_config) *best_config = D->launch_config;
         return LBM_OK;
     }
-    // keep the state: trials run from a copy of the current populations into the other array,
-    // and the copy is restored at the end
-    void* keep = D->dev_alloc(D->pop_bytes());
+    // The state is kept: each configuration runs from a copy of the current populations (and
+    // side buffer), and the copy is restored at the end.
+    const size_t pb = D->pop_bytes(), sb = D->twist() ? D->side_bytes() : 0;
+    unsigned char* keep = static_cast<unsigned char*>(D->dev_alloc(pb + sb));
     if (!keep) return fail(LBM_ERR_OOM, "allocation failed: autotune copy");
-    cudaError_t e = cudaMemcpyAsync(keep, D->d_pop[D->cur], D->pop_bytes(), cudaMemcpyDeviceToDevice, D->stream);
+    cudaError_t e = cudaMemcpyAsync(keep, D->src(), pb, cudaMemcpyDeviceToDevice, D->stream);
+    if (e == cudaSuccess && sb) e = cudaMemcpyAsync(keep + pb, D->d_side, sb, cudaMemcpyDeviceToDevice, D->stream);
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    const LevelArgs a = D->level_args(D->time);
+    const Launchers& L = launchers(D->params.storage);
     int best = D->launch_config;
     float best_ms = INFINITY;
     for (int c = 0; c < N_LAUNCH_CONFIGS && e == cudaSuccess; ++c) {
-        // one untimed launch, then trial_steps alternating launches
-        e = launch_step(D->params.storage, c, D->view, keep, D->d_pop[1 - D->cur], a, D->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(t0, D->stream);
-        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
-            const void* s = (k % 2 == 0) ? D->d_pop[1 - D->cur] : D->d_pop[D->cur];
-            void* d = (k % 2 == 0) ? D->d_pop[D->cur] : D->d_pop[1 - D->cur];
-            e = launch_step(D->params.storage, c, D->view, s, d, a, D->stream);
+        // one untimed step, then trial_steps timed steps, with the level arguments of the
+        // domain's next levels (parity alternates as in a real run)
+        int cur = D->cur;
+        for (int k = 0; k <= trial_steps && e == cudaSuccess; ++k) {
+            if (k == 1) e = cudaEventRecord(t0, D->stream);
+            if (e != cudaSuccess) break;
+            const LevelArgs a = D->level_args(D->time + k);
+            void* src = D->twist() ? D->d_pop[0] : D->d_pop[cur];
+            void* dst = D->twist() ? D->d_pop[0] : D->d_pop[1 - cur];
+            e = L.step(D->params.scheme, c, D->view, src, dst, a, D->stream);
+            cur = 1 - cur;
         }
         if (e == cudaSuccess) e = cudaEventRecord(t1, D->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -561,13 +623,15 @@ lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config
             best_ms = ms;
             best = c;
         }
+        // restore the state for the next configuration
+        if (e == cudaSuccess) e = cudaMemcpyAsync(D->src(), keep, pb, cudaMemcpyDeviceToDevice, D->stream);
+        if (e == cudaSuccess && sb) e = cudaMemcpyAsync(D->d_side, keep + pb, sb, cudaMemcpyDeviceToDevice, D->stream);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(D->d_pop[D->cur], keep, D->pop_bytes(), cudaMemcpyDeviceToDevice, D->stream);
     cudaError_t e2 = cudaStreamSynchronize(D->stream);
     if (e == cudaSuccess) e = e2;
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
-    D->dev_free(keep, D->pop_bytes());
+    D->dev_free(keep, pb + sb);
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     D->launch_config = best;
     if (best_config) *best_config = best;
@@ -594,8 +658,9 @@ lbm_status lbm_get_macroscopic(lbm_domain* D, float* rho, float* u, int32_t dens
     if (dense) e = cudaMemsetAsync(dr, 0, sizeof(float) * n_out, D->stream);
     if (dense && e == cudaSuccess) e = cudaMemsetAsync(du, 0, sizeof(float) * 3 * n_out, D->stream);
     if (e == cudaSuccess)
-        e = launch_macroscopic(D->params.storage, D->view, D->d_pop[D->cur], a, D->d_fl_slot, D->d_fl_box, D->n_fluid,
-                               dense, dr, du, n_out, D->stream);
+        e = launchers(D->params.storage)
+                .macroscopic(D->params.scheme, D->view, D->src(), a, D->d_fl_slot, D->d_fl_box, D->n_fluid, dense, dr,
+                             du, n_out, D->stream);
     if (stage) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, sizeof(float) * n_out, cudaMemcpyDeviceToHost, D->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, sizeof(float) * 3 * n_out, cudaMemcpyDeviceToHost, D->stream);
@@ -612,8 +677,10 @@ lbm_status lbm_get_diagnostics(lbm_domain* D, lbm_diagnostics* out)
     g_last_error.clear();
     if (!D || !out) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
     const LevelArgs a = D->level_args(D->time);
-    cudaError_t e = launch_diagnostics(D->params.storage, D->view, D->d_pop[D->cur], a, D->d_fl_slot, D->n_fluid,
-                                       D->d_partials, D->d_diag, D->stream);
+    cudaError_t e = launchers(D->params.storage)
+                        .diagnostics(D->params.scheme, D->view, D->src(), a, D->d_fl_slot, D->n_fluid, D->d_partials,
+                                     D->stream);
+    if (e == cudaSuccess) e = launch_diagnostics_final(D->d_partials, diagnostics_blocks(D->n_fluid), D->d_diag, D->stream);
     lbm_diagnostics h{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, D->d_diag, sizeof(h), cudaMemcpyDeviceToHost, D->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
@@ -643,6 +710,8 @@ lbm_status lbm_get_info(const lbm_domain* D, lbm_info* out)
     I.bytes_per_value = D->bytes_per_value();
     I.device_bytes = D->device_bytes;
     I.launch_config = D->launch_config;
+    I.scheme = D->params.scheme;
+    I.n_store_bricks = D->n_store_bricks;
     *out = I;
     return LBM_OK;
 }
@@ -675,13 +744,16 @@ lbm_status lbm_save_state(lbm_domain* D, const char* path)
 {
     g_last_error.clear();
     if (!D || !path) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
-    std::vector<unsigned char> buf(D->pop_bytes());
-    cudaError_t e = cudaMemcpyAsync(buf.data(), D->d_pop[D->cur], buf.size(), cudaMemcpyDeviceToHost, D->stream);
+    const size_t sb = D->twist() ? D->side_bytes() : 0;
+    std::vector<unsigned char> buf(D->pop_bytes() + sb);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), D->src(), D->pop_bytes(), cudaMemcpyDeviceToHost, D->stream);
+    if (e == cudaSuccess && sb)
+        e = cudaMemcpyAsync(buf.data() + D->pop_bytes(), D->d_side, sb, cudaMemcpyDeviceToHost, D->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
     if (e != cudaSuccess) return cuda_fail(e, "reading populations");
     CheckpointHeader H{};
     std::memcpy(H.magic, kMagic, 8);
-    H.version = 1;
+    H.version = 2;
     H.nx = D->nx;
     H.ny = D->ny;
     H.nz = D->nz;
@@ -715,12 +787,12 @@ lbm_status lbm_load_state(lbm_domain* D, const char* path)
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     CheckpointHeader H{};
     bool ok = std::fread(&H, sizeof(H), 1, f) == 1;
-    if (!ok || std::memcmp(H.magic, kMagic, 8) != 0 || H.version != 1) {
+    if (!ok || std::memcmp(H.magic, kMagic, 8) != 0 || H.version != 2) {
         std::fclose(f);
         return fail(LBM_ERR_IO, "not a checkpoint of this library");
     }
     if (H.nx != D->nx || H.ny != D->ny || H.nz != D->nz || H.storage != D->params.storage ||
-        H.n_slots != D->n_slots || H.geometry_hash != D->geometry_hash) {
+        H.params.scheme != D->params.scheme || H.n_slots != D->n_slots || H.geometry_hash != D->geometry_hash) {
         std::fclose(f);
         return fail(LBM_ERR_IO, "checkpoint does not match this domain's geometry or storage");
     }
@@ -735,12 +807,15 @@ lbm_status lbm_load_state(lbm_domain* D, const char* path)
         ok = std::fread(wa.data(), sizeof(double), wa.size(), f) == wa.size();
         if (ok && H.n_harm > 0) ok = std::fread(wb.data(), sizeof(double), wb.size(), f) == wb.size();
     }
-    std::vector<unsigned char> buf(D->pop_bytes());
+    const size_t sb = D->twist() ? D->side_bytes() : 0;
+    std::vector<unsigned char> buf(D->pop_bytes() + sb);
     if (ok) ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
     if (!ok) return fail(LBM_ERR_IO, "truncated checkpoint");
     if (lbm_status s = check_params(H.params)) return s;
-    cudaError_t e = cudaMemcpyAsync(D->d_pop[D->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, D->stream);
+    cudaError_t e = cudaMemcpyAsync(D->src(), buf.data(), D->pop_bytes(), cudaMemcpyHostToDevice, D->stream);
+    if (e == cudaSuccess && sb)
+        e = cudaMemcpyAsync(D->d_side, buf.data() + D->pop_bytes(), sb, cudaMemcpyHostToDevice, D->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
     if (e != cudaSuccess) return cuda_fail(e, "writing populations");
     D->params = H.params;

@@ -21,12 +21,17 @@ __host__ __device__ constexpr float w_of(int i)
     return w1_of(cx_of(i)) * w1_of(cy_of(i)) * w1_of(cz_of(i));
 }
 __host__ __device__ constexpr float inv_w_of(int i) { return 1.0f / w_of(i); }
+// corner of the positive part p_i = max(c_i, 0), and of p_opp(i) = max(-c_i, 0): e = px + 2py + 4pz
+__host__ __device__ constexpr int corner_pos(int i) { return (cx_of(i) > 0) + 2 * (cy_of(i) > 0) + 4 * (cz_of(i) > 0); }
+__host__ __device__ constexpr int corner_neg(int i) { return (cx_of(i) < 0) + 2 * (cy_of(i) < 0) + 4 * (cz_of(i) < 0); }
 
 // Geometry is stored in 4x4x4 bricks; a population slot is brick * 64 + lx + 4 ly + 16 lz.
+// Bricks holding fluid ("active", updated every step) come first; the esoteric-twist layout adds
+// the bricks at offsets {0,1}^3 of active bricks ("halo", storage only).
 constexpr int BRICK_EDGE = 4;
 constexpr int BRICK_CELLS = 64;
 
-// Per-slot cell word.
+// Per-slot cell word (active bricks).
 //   bits 0..26  wall mask: bit i set <=> the pull source x - c_i is not a fluid cell
 //   bits 27..28 kind (plain / Bouzidi / inlet / outlet)
 //   bit 31      the slot is a fluid cell (updated every step); solid slots have word 0
@@ -35,14 +40,16 @@ constexpr uint32_t WORD_WALL_MASK = (1u << 27) - 1u;
 constexpr int WORD_KIND_SHIFT = 27;
 enum CellKind { KIND_PLAIN = 0, KIND_BOUZIDI = 1, KIND_INLET = 2, KIND_OUTLET = 3 };
 
-// Read-only geometry of a domain on the device.
+// Geometry of a domain on the device.
 struct DomainView {
-    int64_t n_slots;
-    int64_t n_bricks;
-    const int32_t* nbr;     // [n_bricks][27] brick at offset (ox,oy,oz), index 13 = itself; -1 none
-    const uint32_t* word;   // [n_slots]
-    const int32_t* aux;     // [n_slots] record of a Bouzidi or open-boundary cell
+    int64_t n_slots;        // population stride: 64 * (active + halo bricks)
+    int64_t n_bricks;       // active bricks
+    const int32_t* nbr;     // A-B:  [n_bricks][27] brick at offset (ox,oy,oz) in {-1,0,1}^3, -1 none
+    const int32_t* nb8;     // twist: [n_bricks][8] brick at offset (ex,ey,ez) in {0,1}^3, never -1
+    const uint32_t* word;   // [64 n_bricks]
+    const int32_t* aux;     // [64 n_bricks] record of a Bouzidi or open-boundary cell
     const float* bq;        // [27][n_bq] Bouzidi q of the link whose unknown is i (0: halfway BB)
+    void* side;             // twist: [27][n_bq] f*_i of the previous step at Bouzidi cells (storage type)
     int64_t n_bq;
     const float* io_phi;    // [n_io] inflow profile factor 2 (1 - r^2/R^2)
     const int8_t* io_axis;  // [n_io] inward normal axis
@@ -57,23 +64,34 @@ struct LevelArgs {
     float s2, s3, s4, s5, s6;  // relaxation rates by moment order
     float rho_out;
     float drho_out;  // rho_out - 1, rounded once from FP64
+    int parity;      // n & 1 (esoteric twist)
 };
 
-// Launchers (lbm_kernels.cu).  All enqueue on `stream` and return the launch status.
-constexpr int N_LAUNCH_CONFIGS = 6;
-constexpr int DEFAULT_LAUNCH_CONFIG = 1;  // 256 threads, 3 CTAs per SM
-const char* launch_config_name(int config);
-cudaError_t launch_step(int storage, int config, const DomainView& v, const void* src, void* dst,
+constexpr int N_LAUNCH_CONFIGS = 4;
+constexpr int DEFAULT_LAUNCH_CONFIG = 3;  // 128 threads, 8 CTAs per SM
+
+// Launchers, one set per storage precision (lbm_step_<storage>.cu).  All enqueue on `stream`
+// and return the launch status.
+struct Launchers {
+    cudaError_t (*step)(int scheme, int config, const DomainView& v, const void* src, void* dst,
                         const LevelArgs& a, cudaStream_t stream);
-cudaError_t launch_macroscopic(int storage, const DomainView& v, const void* src, const LevelArgs& a,
-                               const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,
-                               int dense, float* rho, float* u, int64_t n_out, cudaStream_t stream);
-cudaError_t launch_init_equilibrium(int storage, int64_t n_slots, void* dst, const int32_t* fl_slot,
-                                    const int32_t* fl_box, int64_t n_fluid, const float* rho,
-                                    const float* u, int64_t n_box, cudaStream_t stream);
+    cudaError_t (*macroscopic)(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid, int dense,
+                               float* rho, float* u, int64_t n_out, cudaStream_t stream);
+    cudaError_t (*init_equilibrium)(int scheme, const DomainView& v, void* dst, int parity_prev,
+                                    const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,
+                                    const float* rho, const float* u, int64_t n_box, cudaStream_t stream);
+    cudaError_t (*diagnostics)(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, int64_t n_fluid, double* partials, cudaStream_t stream);
+};
+const Launchers& launchers_fp32();
+const Launchers& launchers_fp16();
+const Launchers& launchers_bf16();
+const Launchers& launchers(int storage);
+
 int64_t diagnostics_blocks(int64_t n_fluid);
-cudaError_t launch_diagnostics(int storage, const DomainView& v, const void* src, const LevelArgs& a,
-                               const int32_t* fl_slot, int64_t n_fluid, double* partials,
-                               lbm_diagnostics* out, cudaStream_t stream);
+cudaError_t launch_diagnostics_final(const double* partials, int64_t n_blocks, lbm_diagnostics* out,
+                                     cudaStream_t stream);
+const char* launch_config_name(int config);
 
 }  // namespace lbm

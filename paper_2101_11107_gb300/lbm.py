@@ -23,8 +23,9 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
            "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error", "lbm_set_launch_config",
            "lbm_autotune"]
-N_LAUNCH_CONFIGS = 6
-LAUNCH_CONFIG_NAMES = ["256x2", "256x3", "256x4", "128x6", "128x8", "512x1"]
+N_LAUNCH_CONFIGS = 4
+LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8"]
+SCHEME = {"ab": 0, "esoteric": 1}
 
 
 class LbmError(RuntimeError):
@@ -37,7 +38,7 @@ class Params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("omega_hi", ctypes.c_double * 4),
                 ("force", ctypes.c_double * 3), ("force_amp", ctypes.c_double * 3),
                 ("force_omega", ctypes.c_double), ("rho_out", ctypes.c_double),
-                ("periodic", ctypes.c_int32 * 3), ("storage", ctypes.c_int32)]
+                ("periodic", ctypes.c_int32 * 3), ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -46,7 +47,8 @@ class Info(ctypes.Structure):
                 ("n_wall_cells", ctypes.c_int64), ("n_bouzidi_cells", ctypes.c_int64),
                 ("n_open_cells", ctypes.c_int64), ("time", ctypes.c_int64), ("storage", ctypes.c_int32),
                 ("bytes_per_value", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("launch_config", ctypes.c_int32)]
+                ("launch_config", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("n_store_bricks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -140,7 +142,7 @@ class Domain:
 
     def __init__(self, mask, periodic=(0, 0, 0), links=None, inlet_center=None, inlet_radius=0.0,
                  tau=0.6, omega_hi=(1.0, 1.0, 1.0, 1.0), force=(0.0, 0.0, 0.0), force_amp=(0.0, 0.0, 0.0),
-                 force_omega=0.0, rho_out=1.0, storage="fp32", device=None, stream=None):
+                 force_omega=0.0, rho_out=1.0, storage="fp32", scheme="esoteric", device=None, stream=None):
         import torch
         L = load_library()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -162,6 +164,7 @@ class Domain:
         p.force_omega = force_omega
         p.rho_out = rho_out
         p.storage = STORE[storage] if isinstance(storage, str) else int(storage)
+        p.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
         self.storage = storage
         if links is None or len(links[0]) == 0:
             lc = ld = lq = None
@@ -182,10 +185,10 @@ class Domain:
         self._h = h
 
     @classmethod
-    def from_geometry(cls, g, storage="fp32", **kw):
+    def from_geometry(cls, g, storage="fp32", scheme="esoteric", **kw):
         dom = cls(g.mask, periodic=g.periodic, links=g.links, inlet_center=g.inlet_center,
                   inlet_radius=g.inlet_radius, tau=g.tau, force=g.g0, force_amp=g.gamp,
-                  force_omega=g.gomega, storage=storage, **kw)
+                  force_omega=g.gomega, storage=storage, scheme=scheme, **kw)
         if g.wave is not None:
             a, b, P, up = g.wave
             dom.set_inlet_waveform(a, b, P, up)

@@ -28,10 +28,10 @@ oracle.set_threads(min(16, os.cpu_count() or 1))
 FP32_TOL = 1e-5
 
 
-def run_pair(g, steps, storage="fp32", init=None, ref_mask=None):
+def run_pair(g, steps, storage="fp32", init=None, ref_mask=None, scheme="esoteric"):
     """Advance the GPU domain and the oracle on geometry g; return both macroscopic fields.
     ref_mask: optional smaller z-slab for the oracle (translational invariance)."""
-    dom = lbm.Domain.from_geometry(g, storage=storage)
+    dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme)
     rm = g.mask if ref_mask is None else ref_mask
     links = g.links if ref_mask is None else None
     ref = oracle.Case(rm, periodic=g.periodic, links=links, inlet_center=g.inlet_center,
@@ -56,11 +56,12 @@ def rel_u(u, u_r):
     return float(np.abs(u - u_r).max() / np.abs(u_r).max())
 
 
-def test_poiseuille_pipe_config_full_size():
+@pytest.mark.parametrize("scheme", ["esoteric", "ab"])
+def test_poiseuille_pipe_config_full_size(scheme):
     """Radius-12 pipe, 32x32x64 periodic in z, tau 0.6, g 1e-6, halfway bounce-back, 1000 steps:
     every z-layer of the GPU field against the oracle's one-layer slab."""
     g = I.poiseuille_pipe_32()
-    rho, u, rho_r, u_r = run_pair(g, 1000, ref_mask=g.mask[:1].copy())
+    rho, u, rho_r, u_r = run_pair(g, 1000, ref_mask=g.mask[:1].copy(), scheme=scheme)
     for z in range(g.mask.shape[0]):
         assert rel_u(u[:, z:z + 1], u_r) <= FP32_TOL, z
         assert np.abs(rho[z] - rho_r[0]).max() <= 1e-5
@@ -95,15 +96,15 @@ def test_open_boundaries_pulsatile():
     assert np.abs(rho - rho_r).max() <= 1e-5
 
 
-@pytest.mark.parametrize("seed,edge", [(1, 64), (7, 96)])
-def test_synthetic_aneurysm_downscaled(seed, edge):
+@pytest.mark.parametrize("seed,edge,scheme", [(1, 64, "esoteric"), (7, 96, "esoteric"), (1, 64, "ab")])
+def test_synthetic_aneurysm_downscaled(seed, edge, scheme):
     """The seeded aneurysm generator at a reduced box (all boundary kinds at once: Bouzidi
     walls, inlet waveform, outlet), 400 steps, every cell.  Re 20 keeps the flow laminar at
     this resolution: at Re 300 a 3-cell vessel with tau ~ 0.5015 amplifies a 1e-7 perturbation
     to 1e-2 within 400 steps in the oracle alone, so FP32 and FP64 runs part ways for reasons
     of the flow, not of the arithmetic."""
     g = I.aneurysm(seed, edge=edge, period=400.0, reynolds=20.0)
-    rho, u, rho_r, u_r = run_pair(g, 400)
+    rho, u, rho_r, u_r = run_pair(g, 400, scheme=scheme)
     assert rel_u(u, u_r) <= FP32_TOL
     assert np.abs(rho - rho_r).max() <= 1e-5
 
@@ -198,19 +199,21 @@ def test_open_boundary_flux_diagnostics():
     assert d["flux_in"] > 0 and abs(d["flux_out"] / d["flux_in"] - 1.0) < 2e-2
 
 
-def test_checkpoint_round_trip(tmp_path):
-    """N steps == k steps + save + load into a fresh domain + (N - k) steps, bit for bit."""
+@pytest.mark.parametrize("scheme,k", [("esoteric", 51), ("esoteric", 50), ("ab", 51)])
+def test_checkpoint_round_trip(tmp_path, scheme, k):
+    """N steps == k steps + save + load into a fresh domain + (N - k) steps, bit for bit
+    (odd and even k: the twist stores its populations by level parity)."""
     g = I.aneurysm(2, edge=64, period=200.0)
-    a = lbm.Domain.from_geometry(g)
+    a = lbm.Domain.from_geometry(g, scheme=scheme)
     a.step(120)
     rho_a, u_a = a.macroscopic()
-    b = lbm.Domain.from_geometry(g)
-    b.step(50)
+    b = lbm.Domain.from_geometry(g, scheme=scheme)
+    b.step(k)
     b.save_state(tmp_path / "ck.bin")
-    c = lbm.Domain.from_geometry(g)
+    c = lbm.Domain.from_geometry(g, scheme=scheme)
     c.load_state(tmp_path / "ck.bin")
-    assert c.time == 50
-    c.step(70)
+    assert c.time == k
+    c.step(120 - k)
     rho_c, u_c = c.macroscopic()
     assert np.array_equal(rho_a, rho_c) and np.array_equal(u_a, u_c)
 
@@ -224,3 +227,54 @@ def test_compact_export_matches_dense():
     fl = g.mask.reshape(-1) > 0
     assert np.array_equal(rho.reshape(-1)[fl], rc)
     assert np.array_equal(u.reshape(3, -1)[:, fl], uc)
+
+
+def _fields(g, scheme, storage, steps, reinit_at=None):
+    dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme)
+    if reinit_at is not None:
+        dom.step(reinit_at)
+        rho0, u0 = I.taylor_green(*g.mask.shape[::-1], 0.02)
+        dom.init_equilibrium(rho0, u0)
+    dom.step(steps)
+    rho, u = dom.macroscopic()
+    d = dom.diagnostics()
+    dom.close()
+    return rho, u, d
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_esoteric_twist_equals_ab_bitwise(storage):
+    """The in-place esoteric twist and the two-array A-B scheme run the same arithmetic on the
+    same values, so every stored population -- and hence every exported field -- is identical
+    bit for bit: the aneurysm (Bouzidi q on both branches, inlet, outlet) over an odd number of
+    steps, and a periodic box re-initialised from equilibrium at an odd level."""
+    g = I.aneurysm(3, edge=64, period=200.0, reynolds=30.0)
+    ra, ua, da = _fields(g, "ab", storage, 37)
+    re, ue, de = _fields(g, "esoteric", storage, 37)
+    assert np.array_equal(ra, re) and np.array_equal(ua, ue) and da == de
+    box = I.Geometry(mask=np.ones((8, 16, 12), np.uint8), periodic=(1, 1, 1), tau=0.7, g0=(1e-5, 0, 0))
+    ra, ua, _ = _fields(box, "ab", storage, 9, reinit_at=3)
+    re, ue, _ = _fields(box, "esoteric", storage, 9, reinit_at=3)
+    assert np.array_equal(ra, re) and np.array_equal(ua, ue)
+
+
+def test_autotune_keeps_state():
+    """Autotuning runs every launch configuration on the live domain and restores its state;
+    every configuration gives the same fields."""
+    g = I.aneurysm(4, edge=64, period=200.0)
+    ref = lbm.Domain.from_geometry(g)
+    ref.step(41)
+    r0, u0 = ref.macroscopic()
+    dom = lbm.Domain.from_geometry(g)
+    dom.step(20)
+    best, ms = dom.autotune(5)
+    assert dom.time == 20 and 0 <= best < lbm.N_LAUNCH_CONFIGS and all(v > 0 for v in ms.values())
+    dom.step(21)
+    r1, u1 = dom.macroscopic()
+    assert np.array_equal(r0, r1) and np.array_equal(u0, u1)
+    for c in range(lbm.N_LAUNCH_CONFIGS):
+        d = lbm.Domain.from_geometry(g)
+        d.set_launch_config(c)
+        d.step(41)
+        r2, u2 = d.macroscopic()
+        assert np.array_equal(r0, r2) and np.array_equal(u0, u2)
