@@ -176,6 +176,24 @@ lbm_status lbm_get_macroscopic(lbm_domain* dom, float* rho, float* u, int32_t de
  * non-finite.  The reduction order is fixed, so results are reproducible run to run. */
 lbm_status lbm_get_diagnostics(lbm_domain* dom, lbm_diagnostics* out);
 
+/*
+ * The same reduction as lbm_get_diagnostics, for callers that must not allocate device memory
+ * at the time of the call: a monitoring loop with latency bounds (cudaMalloc may block and
+ * synchronise the device), or an application whose device memory is already reserved in full
+ * by another framework's pool.  It allocates nothing: its scratch is a fixed array of about
+ * 320 KiB inside this library, present on every device that loads the library until the
+ * process exits.  The paper has no counterpart; this is a library service.
+ *   Limit: domains of at most 2,097,152 fluid cells (INVALID_ARG beyond, nothing launched).
+ *   The first call on a device looks up the array's device address with that device current;
+ *   make that first call before any stream capture.
+ *   All calls share the array; calls whose work overlaps on the GPU (domains on different
+ *   streams or host threads) race on it, so serialise them.  Nothing in it needs clearing
+ *   between calls: each call overwrites every word it reads.
+ *   Waits for the domain's stream.  Returns UNSTABLE (after filling *out) on non-finite
+ *   populations, like lbm_get_diagnostics.
+ */
+lbm_status lbm_get_diagnostics_noalloc(lbm_domain* dom, lbm_diagnostics* out);
+
 lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
 
 /* Number of launch configurations of the fused step kernel. */

@@ -840,3 +840,24 @@ void lbm_destroy(lbm_domain* D)
 }
 
 }  // extern "C"
+
+namespace lbm {
+
+bool domain_access(const lbm_domain* D, DomainAccess* out)
+{
+    if (!D || !out) return false;
+    out->storage = D->params.storage;
+    out->scheme = D->params.scheme;
+    out->view = &D->view;
+    out->src = D->src();
+    out->args = D->level_args(D->time);
+    out->fl_slot = D->d_fl_slot;
+    out->n_fluid = D->n_fluid;
+    out->time = D->time;
+    out->stream = D->stream;
+    return true;
+}
+
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+}  // namespace lbm

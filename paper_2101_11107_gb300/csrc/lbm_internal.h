@@ -94,4 +94,19 @@ cudaError_t launch_diagnostics_final(const double* partials, int64_t n_blocks, l
                                      cudaStream_t stream);
 const char* launch_config_name(int config);
 
+// Read access to a domain's device state for entry points defined outside lbm_domain.cu.
+struct DomainAccess {
+    int storage, scheme;
+    const DomainView* view;
+    const void* src;      // populations of the current level
+    LevelArgs args;       // arguments of the current level
+    const int32_t* fl_slot;
+    int64_t n_fluid;
+    int64_t time;
+    cudaStream_t stream;
+};
+bool domain_access(const lbm_domain* dom, DomainAccess* out);
+// sets the calling thread's lbm_last_error() message
+void set_last_error(const char* msg);
+
 }  // namespace lbm

@@ -22,7 +22,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSTABLE", 5: "TIM
 EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium",
            "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
            "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error", "lbm_set_launch_config",
-           "lbm_autotune"]
+           "lbm_autotune", "lbm_get_diagnostics_noalloc"]
 N_LAUNCH_CONFIGS = 4
 LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8"]
 SCHEME = {"ab": 0, "esoteric": 1}
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     L.lbm_step.argtypes = [vp, i64]
     L.lbm_get_macroscopic.argtypes = [vp, vp, vp, i32, i32]
     L.lbm_get_diagnostics.argtypes = [vp, ctypes.POINTER(Diagnostics)]
+    L.lbm_get_diagnostics_noalloc.argtypes = [vp, ctypes.POINTER(Diagnostics)]
     L.lbm_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.lbm_sync.argtypes = [vp]
     L.lbm_save_state.argtypes = [vp, ctypes.c_char_p]
@@ -98,7 +99,8 @@ def load_library(path: str = LIB_PATH):
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
                  "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
-                 "lbm_save_state", "lbm_load_state", "lbm_set_launch_config", "lbm_autotune"]:
+                 "lbm_save_state", "lbm_load_state", "lbm_set_launch_config", "lbm_autotune",
+                 "lbm_get_diagnostics_noalloc"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -274,6 +276,15 @@ class Domain:
         ms = (ctypes.c_float * N_LAUNCH_CONFIGS)()
         _check(load_library().lbm_autotune(self._h, int(trial_steps), ctypes.byref(best), ms))
         return best.value, dict(zip(LAUNCH_CONFIG_NAMES, list(ms)))
+
+    def diagnostics_noalloc(self, raise_unstable=True) -> dict:
+        """lbm_get_diagnostics_noalloc: the same reduction with the library's fixed scratch
+        array, for callers that cannot allocate device memory at that point."""
+        dg = Diagnostics()
+        st = load_library().lbm_get_diagnostics_noalloc(self._h, ctypes.byref(dg))
+        if st != 0 and (raise_unstable or st != 4):
+            _check(st)
+        return dg.as_dict()
 
     def save_state(self, path):
         _check(load_library().lbm_save_state(self._h, os.fsencode(path)))
