@@ -11,8 +11,9 @@
 // GB300 design:
 //   * Populations are SoA, pop[i][slot], slot = brick * 64 + local cell of a 4x4x4 brick; only
 //     bricks with fluid (and, for the twist, their +{0,1}^3 neighbours) are stored.  One thread
-//     per slot, one CTA per BRICKS bricks; the CTA's brick-neighbour rows are staged in shared
-//     memory, so streaming reads no per-cell neighbour index.
+//     per slot, BRICKS bricks per CTA; a warp covers half a brick and hands the brick's
+//     neighbour row out with shuffles, so streaming reads no per-cell neighbour index and the
+//     kernel has no CTA barrier.
 //   * Two streaming schemes, same arithmetic, bitwise-equal results:
 //       A-B (pull from array A, write to array B): 26 neighbour cells per update;
 //       esoteric twist (in place, one array): the thread of cell x touches only the 8 cells
@@ -26,7 +27,9 @@
 //   * Arithmetic is FP32 on deviations d_i = f_i - w_i throughout (moments, transforms,
 //     relaxation, closures): the O(1) rest-state weights never enter a rounding.
 //   * The 27x27 transform runs as three passes of nine 1-D three-point transforms
-//     (T = M(u_x) (x) M(u_y) (x) M(u_z)), forward and inverse, about 500 FP32 flops per cell.
+//     (T = M(u_x) (x) M(u_y) (x) M(u_z)), forward and inverse, about 500 FP32 flops per cell;
+//     with the default rates (third to sixth order = 1) the forward part reduces to the moments
+//     up to second order (about 350 flops per cell in all).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -115,6 +118,41 @@ __device__ __forceinline__ void fetch_ab(const void* __restrict__ src, uint32_t 
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
         d[i] = Store<ST>::load(src, i, off);
+    }
+}
+
+// A-B pull in the step kernel: the brick's 27-entry neighbour row is held by lanes 0..26 of the
+// warp (a warp covers half of one brick) and handed out with shuffles, so no CTA barrier or
+// shared staging is needed.  All 32 lanes run the shuffles; only fluid lanes load.
+template <int ST>
+__device__ __forceinline__ void fetch_ab_shfl(const void* __restrict__ src, uint32_t n, int32_t row_lane,
+                                              uint32_t slot, uint32_t wm, bool fluid, float (&d)[Q])
+{
+    const int l = (int)(slot & (BRICK_CELLS - 1));
+    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
+        const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+        const uint32_t nb = (uint32_t)__shfl_sync(0xffffffffu, row_lane, ob);
+        const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
+        const bool wall = (wm >> i) & 1u;
+        const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
+        if (fluid) d[i] = Store<ST>::load(src, i, off);
+    }
+}
+
+// Twist corner slots in the step kernel: lanes hold the brick's nb8 row (lane & 7).
+__device__ __forceinline__ void corner_slots_shfl(int32_t row_lane, uint32_t slot, uint32_t (&cs)[8])
+{
+    const int l = (int)(slot & (BRICK_CELLS - 1));
+    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int tx = lx + (e & 1), ty = ly + ((e >> 1) & 1), tz = lz + (e >> 2);
+        const int ob = (tx >> 2) | ((ty >> 2) << 1) | ((tz >> 2) << 2);
+        const uint32_t nb = (uint32_t)__shfl_sync(0xffffffffu, row_lane, ob);
+        cs[e] = nb * BRICK_CELLS + (uint32_t)((tx & 3) + ((ty & 3) << 2) + ((tz & 3) << 4));
     }
 }
 
@@ -354,6 +392,87 @@ __device__ __forceinline__ void collide(float (&d)[Q], const LevelArgs& a)
     for (int k = 0; k < 9; ++k) inv3(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, ux2 + CS2);
 }
 
+// The same collision when every third- to sixth-order rate is 1 (the default): the
+// post-collision moments of order >= 3 are then their equilibrium values (zero), so the forward
+// transform is needed only up to second order.  rho - 1, j and the six raw second moments of d
+// come from one pass of 1-D sums (S0 = g- + g0 + g+, S1 = g+ - g-, S2 = g+ + g- along x, then
+// the same along y and z); the central second moments follow from them,
+//   a_200 = P_xx - 2 u_x j_x + (u_x^2 - c_s^2)(rho - 1),
+//   a_110 = P_xy - u_x j_y - u_y j_x + u_x u_y (rho - 1),
+// and the inverse transform is unchanged.  Same arithmetic as `collide` up to rounding order.
+__device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a)
+{
+    float S0[9], S1[9], S2[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        S2[k] = d[3 * k] + d[3 * k + 2];
+        S0[k] = S2[k] + d[3 * k + 1];
+        S1[k] = d[3 * k + 2] - d[3 * k];
+    }
+    float T0[3], T1[3], T2[3], U0[3], U1[3], V[3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+        T2[z] = S0[3 * z] + S0[3 * z + 2];
+        T0[z] = T2[z] + S0[3 * z + 1];
+        T1[z] = S0[3 * z + 2] - S0[3 * z];
+        U0[z] = S1[3 * z] + S1[3 * z + 1] + S1[3 * z + 2];
+        U1[z] = S1[3 * z + 2] - S1[3 * z];
+        V[z] = S2[3 * z] + S2[3 * z + 1] + S2[3 * z + 2];
+    }
+    const float drho = T0[0] + T0[1] + T0[2];
+    const float jz = T0[2] - T0[0];
+    const float Pzz = T0[2] + T0[0];
+    const float jy = T1[0] + T1[1] + T1[2];
+    const float Pyz = T1[2] - T1[0];
+    const float Pyy = T2[0] + T2[1] + T2[2];
+    const float jx = U0[0] + U0[1] + U0[2];
+    const float Pxz = U0[2] - U0[0];
+    const float Pxy = U1[0] + U1[1] + U1[2];
+    const float Pxx = V[0] + V[1] + V[2];
+    const float rho = 1.0f + drho;
+    const float ir = 1.0f / rho;
+    const float ux = fmaf(jx, ir, 0.5f * a.g[0]);
+    const float uy = fmaf(jy, ir, 0.5f * a.g[1]);
+    const float uz = fmaf(jz, ir, 0.5f * a.g[2]);
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const float s2 = a.s2, k2 = 1.0f - a.s2;
+    // central second moments of d, relaxed: b = (1 - s2) a_d - s2 a_w
+    const float a200 = Pxx - 2.0f * ux * jx + (ux2 - CS2) * drho;
+    const float a020 = Pyy - 2.0f * uy * jy + (uy2 - CS2) * drho;
+    const float a002 = Pzz - 2.0f * uz * jz + (uz2 - CS2) * drho;
+    const float a110 = Pxy - ux * jy - uy * jx + ux * uy * drho;
+    const float a101 = Pxz - ux * jz - uz * jx + ux * uz * drho;
+    const float a011 = Pyz - uy * jz - uz * jy + uy * uz * drho;
+    const float ex[3] = {1.0f, -ux, ux2}, ey[3] = {1.0f, -uy, uy2}, ez[3] = {1.0f, -uz, uz2};
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        const int o = order_of(m);
+        const float aw = ex[m % 3] * ey[(m / 3) % 3] * ez[m / 9];
+        if (o >= 3) d[m] = -aw;
+    }
+    d[0] = drho;
+    d[1] = fmaf(0.5f * rho, a.g[0], ux);
+    d[3] = fmaf(0.5f * rho, a.g[1], uy);
+    d[9] = fmaf(0.5f * rho, a.g[2], uz);
+    d[2] = k2 * a200 - s2 * ux2;
+    d[6] = k2 * a020 - s2 * uy2;
+    d[18] = k2 * a002 - s2 * uz2;
+    d[4] = k2 * a110 - s2 * (ux * uy);
+    d[10] = k2 * a101 - s2 * (ux * uz);
+    d[12] = k2 * a011 - s2 * (uy * uz);
+    // inverse T(u)^-1
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) inv3(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, uz2 + CS2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) inv3(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, uy2 + CS2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) inv3(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, ux2 + CS2);
+}
+
 // ------------------------------------------------------------------------------ gather (read-only)
 // Populations of level n of one fluid cell, for the export and diagnostics kernels.
 template <int ST, int SCHEME>
@@ -373,31 +492,29 @@ __device__ __forceinline__ void gather(const DomainView& v, const void* src, uin
 }
 
 // ------------------------------------------------------------------------------ kernels
-template <int ST, int SCHEME, int BRICKS, int MINB>
+template <int ST, int SCHEME, int BRICKS, int MINB, bool FAST>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step(DomainView v, const void* src, void* dst, LevelArgs a)
 {
-    constexpr int NB = (SCHEME == LBM_SCHEME_ESOTERIC) ? 8 : Q;
-    __shared__ int32_t s_nb[BRICKS * NB];
-    const int32_t* table = (SCHEME == LBM_SCHEME_ESOTERIC) ? v.nb8 : v.nbr;
-    const int64_t brick0 = (int64_t)blockIdx.x * BRICKS;
-    for (int t = threadIdx.x; t < BRICKS * NB; t += blockDim.x)
-        s_nb[t] = (brick0 + t / NB < v.n_bricks) ? __ldg(table + brick0 * NB + t) : -1;
-    __syncthreads();
-    const uint32_t slot = (uint32_t)(brick0 * BRICK_CELLS) + threadIdx.x;
+    const uint32_t slot = blockIdx.x * (uint32_t)(BRICKS * BRICK_CELLS) + threadIdx.x;
+    // the active slots are a multiple of 64, so this exit is taken by whole warps
     if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t brick = slot / BRICK_CELLS;
     const uint32_t word = __ldg(v.word + slot);
-    if (!(word & WORD_FLUID)) return;
+    const bool fluid = (word & WORD_FLUID) != 0u;
     const uint32_t wm = word & WORD_WALL_MASK;
     const uint32_t n = (uint32_t)v.n_slots;
-    const int32_t* row = s_nb + (threadIdx.x / BRICK_CELLS) * NB;
     float d[Q];
     if (SCHEME == LBM_SCHEME_ESOTERIC) {
+        const int32_t row = __ldg(v.nb8 + brick * 8u + (lane & 7u));
         uint32_t cs[8];
-        corner_slots(row, slot, cs);
+        corner_slots_shfl(row, slot, cs);
+        if (!fluid) return;
         fetch_et<ST, true>(dst, n, cs, wm, a.parity, d);
         const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
-        collide(d, a);
+        if (FAST) collide_fast(d, a);
+        else collide(d, a);
         store_et<ST>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t rec = (uint32_t)v.aux[slot];
@@ -407,9 +524,12 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
                 if (half & (1u << i)) Store<ST>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
         }
     } else {
-        fetch_ab<ST>(src, n, row, slot, wm, d);
+        const int32_t row = __ldg(v.nbr + brick * (uint32_t)Q + (lane < (uint32_t)Q ? lane : 0u));
+        fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
+        if (!fluid) return;
         if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
-        collide(d, a);
+        if (FAST) collide_fast(d, a);
+        else collide(d, a);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
     }
@@ -556,7 +676,11 @@ template <int ST, int SCHEME, int BRICKS, int MINB>
 cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const LevelArgs& a, cudaStream_t s)
 {
     if (v.n_bricks == 0) return cudaSuccess;
-    k_step<ST, SCHEME, BRICKS, MINB><<<grid_for(v.n_bricks, BRICKS), BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+    const int grid = grid_for(v.n_bricks, BRICKS);
+    if (a.fast_rates)
+        k_step<ST, SCHEME, BRICKS, MINB, true><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+    else
+        k_step<ST, SCHEME, BRICKS, MINB, false><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
     return cudaGetLastError();
 }
 

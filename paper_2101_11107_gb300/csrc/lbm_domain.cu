@@ -121,6 +121,8 @@ struct lbm_domain {
         a.rho_out = (float)params.rho_out;
         a.drho_out = (float)(params.rho_out - 1.0);
         a.parity = (int)(n & 1);
+        a.fast_rates = (params.omega_hi[0] == 1.0 && params.omega_hi[1] == 1.0 && params.omega_hi[2] == 1.0 &&
+                        params.omega_hi[3] == 1.0) ? 1 : 0;
         return a;
     }
 };

@@ -65,6 +65,7 @@ struct LevelArgs {
     float rho_out;
     float drho_out;  // rho_out - 1, rounded once from FP64
     int parity;      // n & 1 (esoteric twist)
+    int fast_rates;  // every 3rd..6th-order rate is 1: the step kernel skips those moments
 };
 
 constexpr int N_LAUNCH_CONFIGS = 4;
