@@ -692,7 +692,8 @@ cudaError_t launch_step_scheme(int config, const DomainView& v, const void* src,
     case 0: return launch_step_t<ST, SCHEME, 4, 3>(v, src, dst, a, s);
     case 1: return launch_step_t<ST, SCHEME, 4, 4>(v, src, dst, a, s);
     case 2: return launch_step_t<ST, SCHEME, 2, 6>(v, src, dst, a, s);
-    default: return launch_step_t<ST, SCHEME, 2, 8>(v, src, dst, a, s);
+    case 3: return launch_step_t<ST, SCHEME, 2, 8>(v, src, dst, a, s);
+    default: return launch_step_t<ST, SCHEME, 2, 10>(v, src, dst, a, s);
     }
 }
 

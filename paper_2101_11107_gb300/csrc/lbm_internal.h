@@ -68,7 +68,7 @@ struct LevelArgs {
     int fast_rates;  // every 3rd..6th-order rate is 1: the step kernel skips those moments
 };
 
-constexpr int N_LAUNCH_CONFIGS = 4;
+constexpr int N_LAUNCH_CONFIGS = 5;
 constexpr int DEFAULT_LAUNCH_CONFIG = 3;  // 128 threads, 8 CTAs per SM
 
 // Launchers, one set per storage precision (lbm_step_<storage>.cu).  All enqueue on `stream`

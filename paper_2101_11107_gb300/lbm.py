@@ -23,8 +23,8 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
            "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error", "lbm_set_launch_config",
            "lbm_autotune", "lbm_get_diagnostics_noalloc"]
-N_LAUNCH_CONFIGS = 4
-LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8"]
+N_LAUNCH_CONFIGS = 5
+LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10"]
 SCHEME = {"ab": 0, "esoteric": 1}
 
 

@@ -1,0 +1,40 @@
+"""Run a named workload for a few steps on the GPU (for profiling and quick checks).
+
+    python -m paper_2101_11107_gb300.run_case womersley fp32 4 [esoteric|ab]
+    python -m paper_2101_11107_gb300.run_case aneurysm256 fp16 10
+
+Workloads: womersley (64x64x256 pulsatile pipe, radius 28), poiseuille (32x32x64 pipe,
+radius 12), aneurysm256 / aneurysm512 (seeded synthetic aneurysm, seed 11).
+"""
+import sys
+
+
+def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
+    case = argv[0] if argv else "womersley"
+    storage = argv[1] if len(argv) > 1 else "fp32"
+    steps = int(argv[2]) if len(argv) > 2 else 4
+    scheme = argv[3] if len(argv) > 3 else "esoteric"
+    from . import build as lib_build
+    from . import inputs as I
+    from . import lbm
+
+    lib_build.build()
+    if case == "womersley":
+        g = I.womersley_pipe()
+    elif case == "poiseuille":
+        g = I.poiseuille_pipe_32()
+    elif case.startswith("aneurysm"):
+        g = I.aneurysm(11, edge=int(case[len("aneurysm"):] or 256))
+    else:
+        raise SystemExit(f"unknown case {case}")
+    dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme)
+    dom.step(steps)
+    dom.sync()
+    info = dom.info()
+    print(f"ok {case} {storage} {scheme} steps={steps} fluid={info['n_fluid']} slots={info['n_slots']} "
+          f"config={lbm.LAUNCH_CONFIG_NAMES[info['launch_config']]}")
+
+
+if __name__ == "__main__":
+    main()
