@@ -211,6 +211,30 @@ lbm_status lbm_set_launch_config(lbm_domain* dom, int32_t config);
  * runs.  Errors: INVALID_ARG, OOM, CUDA. */
 lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_config, float* ms_per_step);
 
+/*
+ * Batches: several domains advanced together, one kernel launch per step over all of them
+ * (a concatenated brick work list), with chunks of graph_steps steps captured once into a CUDA
+ * graph and replayed (the per-step force and inflow of every domain are uploaded by the graph's
+ * first node).  Results are bit-identical to stepping each domain alone.
+ *   lbm_batch_create: doms[n] (1..4096 distinct domains, esoteric twist, one storage precision,
+ *     all or none with unit higher-order rates) stay owned by the caller and must outlive the
+ *     batch; graph_steps in 1..4096; cuda_stream (NULL: legacy default) runs the batch's work,
+ *     ordered after / before each domain's own stream by events.  Small tables are allocated
+ *     through doms[0]'s allocator.  Errors: INVALID_ARG, OOM, CUDA.
+ *   lbm_batch_step: n >= 0 steps of every domain (each domain's time advances by n); waits for
+ *     the previous chunk before refilling its host argument table.
+ *   lbm_batch_set_launch_config / lbm_batch_autotune: as for single domains; autotune keeps every
+ *     domain's state (it copies and restores the populations) and needs trial_steps <=
+ *     graph_steps.
+ */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_steps, void* cuda_stream,
+                            lbm_batch** out);
+lbm_status lbm_batch_step(lbm_batch* batch, int64_t n);
+lbm_status lbm_batch_set_launch_config(lbm_batch* batch, int32_t config);
+lbm_status lbm_batch_autotune(lbm_batch* batch, int32_t trial_steps, int32_t* best_config, float* ms_per_step);
+void lbm_batch_destroy(lbm_batch* batch);
+
 /* Waits for all work enqueued on the domain. */
 lbm_status lbm_sync(lbm_domain* dom);
 

@@ -492,14 +492,12 @@ __device__ __forceinline__ void gather(const DomainView& v, const void* src, uin
 }
 
 // ------------------------------------------------------------------------------ kernels
-template <int ST, int SCHEME, int BRICKS, int MINB, bool FAST>
-__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
-    k_step(DomainView v, const void* src, void* dst, LevelArgs a)
+// One fused update of the cell at `slot` (a lane of a warp that covers half of one brick; all
+// 32 lanes must call it together: the neighbour row goes round by shuffle).
+template <int ST, int SCHEME, bool FAST>
+__device__ __forceinline__ void step_cell(const DomainView& v, const void* src, void* dst, const LevelArgs& a,
+                                          uint32_t slot, uint32_t lane)
 {
-    const uint32_t slot = blockIdx.x * (uint32_t)(BRICKS * BRICK_CELLS) + threadIdx.x;
-    // the active slots are a multiple of 64, so this exit is taken by whole warps
-    if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
-    const uint32_t lane = threadIdx.x & 31u;
     const uint32_t brick = slot / BRICK_CELLS;
     const uint32_t word = __ldg(v.word + slot);
     const bool fluid = (word & WORD_FLUID) != 0u;
@@ -533,6 +531,39 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
     }
+}
+
+template <int ST, int SCHEME, int BRICKS, int MINB, bool FAST>
+__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
+    k_step(DomainView v, const void* src, void* dst, LevelArgs a)
+{
+    const uint32_t slot = blockIdx.x * (uint32_t)(BRICKS * BRICK_CELLS) + threadIdx.x;
+    // the active slots are a multiple of 64, so this exit is taken by whole warps
+    if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
+    step_cell<ST, SCHEME, FAST>(v, src, dst, a, slot, threadIdx.x & 31u);
+}
+
+// Several domains (esoteric twist, one storage precision) in one launch: the CTAs run over the
+// concatenated brick lists; each warp finds its domain by binary search in the brick prefix
+// sums and updates one of that domain's half-bricks with the domain's own level arguments.
+template <int ST, int BRICKS, int MINB, bool FAST>
+__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
+    k_step_batch(const BatchEntry* __restrict__ ent, const int64_t* __restrict__ brick_start, int n_dom,
+                 const LevelArgs* __restrict__ args)
+{
+    const int64_t gslot = (int64_t)blockIdx.x * (BRICKS * BRICK_CELLS) + threadIdx.x;
+    const int64_t gbrick = gslot / BRICK_CELLS;
+    if (gbrick >= __ldg(brick_start + n_dom)) return;  // whole warps
+    int lo = 0, hi = n_dom - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(brick_start + mid) <= gbrick) lo = mid;
+        else hi = mid - 1;
+    }
+    const DomainView v = ent[lo].view;
+    const LevelArgs a = args[lo];
+    const uint32_t slot = (uint32_t)((gbrick - __ldg(brick_start + lo)) * BRICK_CELLS) + (threadIdx.x & 63u);
+    step_cell<ST, LBM_SCHEME_ESOTERIC, FAST>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
 }
 
 template <int ST, int SCHEME>
@@ -747,11 +778,37 @@ cudaError_t launch_diagnostics(int scheme, const DomainView& v, const void* src,
     return cudaGetLastError();
 }
 
+template <int ST, int BRICKS, int MINB>
+cudaError_t launch_step_batch_t(const BatchEntry* ent, const int64_t* brick_start, int n_dom, int64_t total_bricks,
+                                const LevelArgs* args, int fast, cudaStream_t s)
+{
+    if (total_bricks == 0) return cudaSuccess;
+    const int grid = grid_for(total_bricks, BRICKS);
+    if (fast)
+        k_step_batch<ST, BRICKS, MINB, true><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
+    else
+        k_step_batch<ST, BRICKS, MINB, false><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
+                              int64_t total_bricks, const LevelArgs* args, int fast, cudaStream_t s)
+{
+    switch (config) {
+    case 0: return launch_step_batch_t<ST, 4, 3>(ent, brick_start, n_dom, total_bricks, args, fast, s);
+    case 1: return launch_step_batch_t<ST, 4, 4>(ent, brick_start, n_dom, total_bricks, args, fast, s);
+    case 2: return launch_step_batch_t<ST, 2, 6>(ent, brick_start, n_dom, total_bricks, args, fast, s);
+    case 3: return launch_step_batch_t<ST, 2, 8>(ent, brick_start, n_dom, total_bricks, args, fast, s);
+    default: return launch_step_batch_t<ST, 2, 10>(ent, brick_start, n_dom, total_bricks, args, fast, s);
+    }
+}
+
 template <int ST>
 const Launchers& make_launchers()
 {
     static const Launchers L = {&launch_step<ST>, &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
-                                &launch_diagnostics<ST>};
+                                &launch_diagnostics<ST>, &launch_step_batch<ST>};
     return L;
 }
 

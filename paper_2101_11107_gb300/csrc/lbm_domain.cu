@@ -92,7 +92,7 @@ struct lbm_domain {
         auto it = std::find(owned.begin(), owned.end(), p);
         if (it == owned.end()) return;
         owned.erase(it);
-        device_bytes -= (int64_t)(((bytes + 255) & ~(size_t)255) ? ((bytes + 255) & ~(size_t)255) : 256);
+        if (bytes) device_bytes -= (int64_t)((bytes + 255) & ~(size_t)255);
         if (release) release(p, alloc_ctx);
         else if (!alloc) cudaFree(p);
     }
@@ -839,6 +839,261 @@ void lbm_destroy(lbm_domain* D)
     cudaStreamSynchronize(D->stream);
     D->release_all();
     delete D;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------ batches
+struct lbm_batch {
+    std::vector<lbm_domain*> doms;
+    int storage = 0;
+    int fast = 1;
+    int launch_config = DEFAULT_LAUNCH_CONFIG;
+    int graph_steps = 0;
+    int64_t total_bricks = 0, total_fluid = 0;
+    cudaStream_t stream = nullptr;
+    lbm_domain* owner = nullptr;  // its allocator serves the batch's buffers
+    BatchEntry* d_ent = nullptr;
+    int64_t* d_start = nullptr;
+    LevelArgs* d_args = nullptr;  // [graph_steps][n]
+    LevelArgs* h_args = nullptr;  // pinned mirror
+    size_t args_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    int exec_config = -1;
+    cudaEvent_t ev = nullptr;
+
+    int n() const { return (int)doms.size(); }
+    void fill_args(int steps)
+    {
+        for (int k = 0; k < steps; ++k)
+            for (int d = 0; d < n(); ++d) h_args[(size_t)k * n() + d] = doms[(size_t)d]->level_args(doms[(size_t)d]->time + k);
+    }
+    // orders the batch's stream after, or before, the work of every member domain's stream
+    cudaError_t join_from_domains()
+    {
+        for (lbm_domain* D : doms) {
+            if (D->stream == stream) continue;
+            cudaError_t e = cudaEventRecord(ev, D->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t join_to_domains()
+    {
+        cudaError_t e = cudaEventRecord(ev, stream);
+        for (lbm_domain* D : doms) {
+            if (e != cudaSuccess) break;
+            if (D->stream != stream) e = cudaStreamWaitEvent(D->stream, ev, 0);
+        }
+        return e;
+    }
+    cudaError_t enqueue_steps(int steps, int config)
+    {
+        cudaError_t e = cudaMemcpyAsync(d_args, h_args, sizeof(LevelArgs) * (size_t)steps * n(), cudaMemcpyHostToDevice,
+                                        stream);
+        const Launchers& L = launchers(storage);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k)
+            e = L.step_batch(config, d_ent, d_start, n(), total_bricks, d_args + (size_t)k * n(), fast, stream);
+        return e;
+    }
+    cudaError_t capture()
+    {
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        e = enqueue_steps(graph_steps, launch_config);
+        cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        exec_config = (e == cudaSuccess) ? launch_config : -1;
+        return e;
+    }
+    void release()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ev) cudaEventDestroy(ev);
+        if (h_args) cudaFreeHost(h_args);
+        for (void* p : {(void*)d_ent, (void*)d_start, (void*)d_args})
+            if (p) owner->dev_free(p, 0);
+    }
+};
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_steps, void* cuda_stream,
+                            lbm_batch** out)
+{
+    g_last_error.clear();
+    if (!out) return fail(LBM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!doms || n < 1 || n > 4096) return fail(LBM_ERR_INVALID_ARG, "need 1..4096 domains");
+    if (graph_steps < 1 || graph_steps > 4096) return fail(LBM_ERR_INVALID_ARG, "graph_steps must be in 1..4096");
+    for (int d = 0; d < n; ++d) {
+        if (!doms[d]) return fail(LBM_ERR_INVALID_ARG, "NULL domain in the batch");
+        if (doms[d]->params.scheme != LBM_SCHEME_ESOTERIC)
+            return fail(LBM_ERR_INVALID_ARG, "batched domains must use the esoteric-twist scheme");
+        if (doms[d]->params.storage != doms[0]->params.storage)
+            return fail(LBM_ERR_INVALID_ARG, "batched domains must share one storage precision");
+        if (doms[d]->level_args(0).fast_rates != doms[0]->level_args(0).fast_rates)
+            return fail(LBM_ERR_INVALID_ARG, "batched domains must all use, or all not use, unit higher-order rates");
+        for (int e = 0; e < d; ++e)
+            if (doms[e] == doms[d]) return fail(LBM_ERR_INVALID_ARG, "a domain appears twice in the batch");
+    }
+    lbm_batch* B = new (std::nothrow) lbm_batch();
+    if (!B) return fail(LBM_ERR_OOM, "host allocation failed");
+    B->doms.assign(doms, doms + n);
+    B->storage = doms[0]->params.storage;
+    B->fast = doms[0]->level_args(0).fast_rates;
+    B->graph_steps = graph_steps;
+    B->stream = static_cast<cudaStream_t>(cuda_stream);
+    B->owner = doms[0];
+    std::vector<BatchEntry> ent((size_t)n);
+    std::vector<int64_t> start((size_t)n + 1, 0);
+    for (int d = 0; d < n; ++d) {
+        ent[(size_t)d].view = doms[d]->view;
+        ent[(size_t)d].pop = doms[d]->d_pop[0];
+        start[(size_t)d + 1] = start[(size_t)d] + doms[d]->n_bricks;
+        B->total_fluid += doms[d]->n_fluid;
+    }
+    B->total_bricks = start[(size_t)n];
+    B->args_bytes = sizeof(LevelArgs) * (size_t)graph_steps * (size_t)n;
+    cudaError_t e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_args, B->args_bytes);
+    lbm_status st = (e == cudaSuccess) ? LBM_OK : cuda_fail(e, "batch set-up");
+    if (!st) {
+        B->d_ent = static_cast<BatchEntry*>(B->owner->dev_alloc(sizeof(BatchEntry) * (size_t)n));
+        B->d_start = static_cast<int64_t*>(B->owner->dev_alloc(sizeof(int64_t) * ((size_t)n + 1)));
+        B->d_args = static_cast<LevelArgs*>(B->owner->dev_alloc(B->args_bytes));
+        if (!B->d_ent || !B->d_start || !B->d_args) st = fail(LBM_ERR_OOM, "allocation failed: batch tables");
+    }
+    if (!st) {
+        e = cudaMemcpyAsync(B->d_ent, ent.data(), sizeof(BatchEntry) * ent.size(), cudaMemcpyHostToDevice, B->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(B->d_start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice,
+                                B->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "uploading the batch tables");
+    }
+    if (st) {
+        B->release();
+        delete B;
+        return st;
+    }
+    *out = B;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* B, int64_t n)
+{
+    g_last_error.clear();
+    if (!B) return fail(LBM_ERR_INVALID_ARG, "NULL batch");
+    if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return LBM_OK;
+    cudaError_t e = B->join_from_domains();
+    while (n > 0 && e == cudaSuccess) {
+        const int k = (int)std::min<int64_t>(n, B->graph_steps);
+        // the pinned argument table is reused: wait until the previous chunk has read it
+        e = cudaStreamSynchronize(B->stream);
+        if (e != cudaSuccess) break;
+        B->fill_args(k);
+        if (k == B->graph_steps) {
+            if (!B->exec || B->exec_config != B->launch_config) e = B->capture();
+            if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
+        } else {
+            e = B->enqueue_steps(k, B->launch_config);
+        }
+        if (e == cudaSuccess)
+            for (lbm_domain* D : B->doms) D->time += k;
+        n -= k;
+    }
+    if (e == cudaSuccess) e = B->join_to_domains();
+    if (e != cudaSuccess) return cuda_fail(e, "batch step");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_launch_config(lbm_batch* B, int32_t config)
+{
+    g_last_error.clear();
+    if (!B) return fail(LBM_ERR_INVALID_ARG, "NULL batch");
+    if (config < 0 || config >= N_LAUNCH_CONFIGS) return fail(LBM_ERR_INVALID_ARG, "launch config out of range");
+    B->launch_config = config;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* B, int32_t trial_steps, int32_t* best_config, float* ms_per_step)
+{
+    g_last_error.clear();
+    if (!B || trial_steps < 1 || trial_steps > B->graph_steps)
+        return fail(LBM_ERR_INVALID_ARG, "trial_steps must be in 1..graph_steps");
+    // keep every member's populations and side buffer; run each configuration; restore
+    std::vector<std::pair<void*, size_t>> keep;
+    cudaError_t e = B->join_from_domains();
+    lbm_status st = LBM_OK;
+    for (lbm_domain* D : B->doms) {
+        const size_t bytes = D->pop_bytes() + D->side_bytes();
+        unsigned char* p = static_cast<unsigned char*>(B->owner->dev_alloc(bytes));
+        if (!p) {
+            st = fail(LBM_ERR_OOM, "allocation failed: batch autotune copy");
+            break;
+        }
+        keep.push_back({p, bytes});
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p, D->d_pop[0], D->pop_bytes(), cudaMemcpyDeviceToDevice, B->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p + D->pop_bytes(), D->d_side, D->side_bytes(), cudaMemcpyDeviceToDevice, B->stream);
+    }
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (!st && e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (!st && e == cudaSuccess) e = cudaEventCreate(&t1);
+    int best = B->launch_config;
+    float best_ms = INFINITY;
+    if (!st && e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+    if (!st && e == cudaSuccess) B->fill_args(trial_steps);
+    for (int c = 0; c < N_LAUNCH_CONFIGS && !st && e == cudaSuccess; ++c) {
+        e = B->enqueue_steps(1, c);  // untimed
+        if (e == cudaSuccess) e = cudaEventRecord(t0, B->stream);
+        if (e == cudaSuccess) e = B->enqueue_steps(trial_steps, c);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, B->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        ms /= (float)trial_steps;
+        if (ms_per_step) ms_per_step[c] = ms;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+        for (size_t d = 0; d < keep.size() && e == cudaSuccess; ++d) {
+            lbm_domain* D = B->doms[d];
+            unsigned char* p = static_cast<unsigned char*>(keep[d].first);
+            e = cudaMemcpyAsync(D->d_pop[0], p, D->pop_bytes(), cudaMemcpyDeviceToDevice, B->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(D->d_side, p + D->pop_bytes(), D->side_bytes(), cudaMemcpyDeviceToDevice, B->stream);
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(B->stream);
+    if (e == cudaSuccess) e = e2;
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    for (auto& k : keep) B->owner->dev_free(k.first, k.second);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+    B->launch_config = best;
+    if (best_config) *best_config = best;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* B)
+{
+    if (!B) return;
+    cudaStreamSynchronize(B->stream);
+    B->release();
+    delete B;
 }
 
 }  // extern "C"

@@ -68,6 +68,12 @@ struct LevelArgs {
     int fast_rates;  // every 3rd..6th-order rate is 1: the step kernel skips those moments
 };
 
+// One domain of a batched launch.
+struct BatchEntry {
+    DomainView view;
+    void* pop;  // the domain's in-place population array
+};
+
 constexpr int N_LAUNCH_CONFIGS = 5;
 constexpr int DEFAULT_LAUNCH_CONFIG = 3;  // 128 threads, 8 CTAs per SM
 
@@ -84,6 +90,9 @@ struct Launchers {
                                     const float* rho, const float* u, int64_t n_box, cudaStream_t stream);
     cudaError_t (*diagnostics)(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
                                const int32_t* fl_slot, int64_t n_fluid, double* partials, cudaStream_t stream);
+    // twist only: every domain of the batch one step; args[d] are domain d's level arguments
+    cudaError_t (*step_batch)(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
+                              int64_t total_bricks, const LevelArgs* args, int fast, cudaStream_t stream);
 };
 const Launchers& launchers_fp32();
 const Launchers& launchers_fp16();

@@ -22,7 +22,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSTABLE", 5: "TIM
 EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium",
            "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
            "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error", "lbm_set_launch_config",
-           "lbm_autotune", "lbm_get_diagnostics_noalloc"]
+           "lbm_autotune", "lbm_get_diagnostics_noalloc", "lbm_batch_create", "lbm_batch_step",
+           "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_batch_destroy"]
 N_LAUNCH_CONFIGS = 5
 LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10"]
 SCHEME = {"ab": 0, "esoteric": 1}
@@ -95,12 +96,19 @@ def load_library(path: str = LIB_PATH):
     L.lbm_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp, ctypes.POINTER(vp)]
+    L.lbm_batch_step.argtypes = [vp, i64]
+    L.lbm_batch_set_launch_config.argtypes = [vp, i32]
+    L.lbm_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
                  "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
                  "lbm_save_state", "lbm_load_state", "lbm_set_launch_config", "lbm_autotune",
-                 "lbm_get_diagnostics_noalloc"]:
+                 "lbm_get_diagnostics_noalloc", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_batch_set_launch_config", "lbm_batch_autotune"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -291,3 +299,46 @@ class Domain:
 
     def load_state(self, path):
         _check(load_library().lbm_load_state(self._h, os.fsencode(path)))
+
+
+class Batch:
+    """Several domains advanced together (one launch per step over all of them, chunks of
+    graph_steps steps replayed as a CUDA graph); see lbm_batch_* in include/lbm.h."""
+
+    def __init__(self, domains, graph_steps=50, stream=None):
+        import torch
+        L = load_library()
+        self.domains = list(domains)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        arr = (ctypes.c_void_p * len(self.domains))(*[d._h.value for d in self.domains])
+        h = ctypes.c_void_p()
+        _check(L.lbm_batch_create(arr, len(self.domains), int(graph_steps),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, n=1):
+        _check(load_library().lbm_batch_step(self._h, int(n)))
+
+    def set_launch_config(self, config):
+        _check(load_library().lbm_batch_set_launch_config(self._h, int(config)))
+
+    def autotune(self, trial_steps=20):
+        best = ctypes.c_int32()
+        ms = (ctypes.c_float * N_LAUNCH_CONFIGS)()
+        _check(load_library().lbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(best), ms))
+        return best.value, dict(zip(LAUNCH_CONFIG_NAMES, list(ms)))
+
+    @property
+    def n_fluid(self):
+        return sum(d.info()["n_fluid"] for d in self.domains)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
