@@ -218,9 +218,11 @@ lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_conf
  * first node).  Results are bit-identical to stepping each domain alone.
  *   lbm_batch_create: doms[n] (1..4096 distinct domains, esoteric twist, one storage precision,
  *     all or none with unit higher-order rates) stay owned by the caller and must outlive the
- *     batch; graph_steps in 1..4096; cuda_stream (NULL: legacy default) runs the batch's work,
- *     ordered after / before each domain's own stream by events.  Small tables are allocated
- *     through doms[0]'s allocator.  Errors: INVALID_ARG, OOM, CUDA.
+ *     batch; graph_steps in 1..4096.  The batch runs (and captures) its work on a private
+ *     non-blocking stream, ordered by events after the work already enqueued on cuda_stream
+ *     (NULL: legacy default) and on each domain's stream, and before anything enqueued there
+ *     later.  Small tables are allocated through doms[0]'s allocator.  Errors: INVALID_ARG, OOM,
+ *     CUDA.
  *   lbm_batch_step: n >= 0 steps of every domain (each domain's time advances by n); waits for
  *     the previous chunk before refilling its host argument table.
  *   lbm_batch_set_launch_config / lbm_batch_autotune: as for single domains; autotune keeps every

@@ -851,7 +851,8 @@ struct lbm_batch {
     int launch_config = DEFAULT_LAUNCH_CONFIG;
     int graph_steps = 0;
     int64_t total_bricks = 0, total_fluid = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // private non-blocking stream: work and graph capture
+    cudaStream_t user_stream = nullptr;  // the caller's stream, ordered before and after
     lbm_domain* owner = nullptr;  // its allocator serves the batch's buffers
     BatchEntry* d_ent = nullptr;
     int64_t* d_start = nullptr;
@@ -871,20 +872,22 @@ struct lbm_batch {
     // orders the batch's stream after, or before, the work of every member domain's stream
     cudaError_t join_from_domains()
     {
+        cudaError_t e = cudaEventRecord(ev, user_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
         for (lbm_domain* D : doms) {
-            if (D->stream == stream) continue;
-            cudaError_t e = cudaEventRecord(ev, D->stream);
+            if (e != cudaSuccess) break;
+            e = cudaEventRecord(ev, D->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev, 0);
-            if (e != cudaSuccess) return e;
         }
-        return cudaSuccess;
+        return e;
     }
     cudaError_t join_to_domains()
     {
         cudaError_t e = cudaEventRecord(ev, stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(user_stream, ev, 0);
         for (lbm_domain* D : doms) {
             if (e != cudaSuccess) break;
-            if (D->stream != stream) e = cudaStreamWaitEvent(D->stream, ev, 0);
+            e = cudaStreamWaitEvent(D->stream, ev, 0);
         }
         return e;
     }
@@ -918,6 +921,7 @@ struct lbm_batch {
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (ev) cudaEventDestroy(ev);
+        if (stream) cudaStreamDestroy(stream);
         if (h_args) cudaFreeHost(h_args);
         for (void* p : {(void*)d_ent, (void*)d_start, (void*)d_args})
             if (p) owner->dev_free(p, 0);
@@ -951,7 +955,7 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
     B->storage = doms[0]->params.storage;
     B->fast = doms[0]->level_args(0).fast_rates;
     B->graph_steps = graph_steps;
-    B->stream = static_cast<cudaStream_t>(cuda_stream);
+    B->user_stream = static_cast<cudaStream_t>(cuda_stream);
     B->owner = doms[0];
     std::vector<BatchEntry> ent((size_t)n);
     std::vector<int64_t> start((size_t)n + 1, 0);
@@ -963,7 +967,8 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
     }
     B->total_bricks = start[(size_t)n];
     B->args_bytes = sizeof(LevelArgs) * (size_t)graph_steps * (size_t)n;
-    cudaError_t e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+    cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_args, B->args_bytes);
     lbm_status st = (e == cudaSuccess) ? LBM_OK : cuda_fail(e, "batch set-up");
     if (!st) {
@@ -978,6 +983,8 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
             e = cudaMemcpyAsync(B->d_start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice,
                                 B->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+        // the domains' buffers were cleared / uploaded on their own streams
+        for (int d = 0; d < n && e == cudaSuccess; ++d) e = cudaStreamSynchronize(doms[d]->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "uploading the batch tables");
     }
     if (st) {
@@ -1081,6 +1088,7 @@ lbm_status lbm_batch_autotune(lbm_batch* B, int32_t trial_steps, int32_t* best_c
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     for (auto& k : keep) B->owner->dev_free(k.first, k.second);
+    if (e == cudaSuccess) e = B->join_to_domains();
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
     B->launch_config = best;
