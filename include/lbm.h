@@ -237,6 +237,49 @@ lbm_status lbm_batch_set_launch_config(lbm_batch* batch, int32_t config);
 lbm_status lbm_batch_autotune(lbm_batch* batch, int32_t trial_steps, int32_t* best_config, float* ms_per_step);
 void lbm_batch_destroy(lbm_batch* batch);
 
+/*
+ * Learned coarse-grid corrector (not part of the paper: its Sec. 3.4 shows that a 2x coarser
+ * grid keeps useful accuracy at ~14x less cost; the corrector nudges the coarse velocity toward
+ * the fine solution restricted onto the coarse grid).  A 3-layer 3-D convolutional network,
+ * 16 channels, 3x3x3 kernels, zero padding, ReLU, BF16 weights and activations with FP32
+ * accumulation on the tensor cores, evaluated on the 4^3 tiles near fluid:
+ *   X0 = [u/u_scale (3), (rho-1)/rho_scale, fluid mask, 0 (11)]  (zero at solid cells)
+ *   O  = conv3(relu(conv2(relu(conv1(X0)))));  du = du_scale * O[0:3] at fluid cells.
+ * Parameters (FP32, lbm_corrector_num_params() of them): W1[27][16][16], b1[16], W2, b2, W3, b3
+ * with W[o][out][in], offset o = (dx+1) + 3(dy+1) + 9(dz+1).
+ *   lbm_corrector_create: mask[nx*ny*nz] (nonzero = fluid) of the coarse box (extents multiples
+ *     of 4); the scales; initial params (copied).  Memory through the allocator callbacks.
+ *   lbm_corrector_forward: rho[n], u[3][n] dense device fields -> du[3][n] device.
+ *   lbm_corrector_gradients: loss L = mean over fluid cells and components of
+ *     (O[0:3] - (u_target - u)/du_scale)^2 and dL/dparams (host, FP32); waits.
+ *   lbm_corrector_train_step: the same, then one Adam step (b1 0.9, b2 0.999, eps 1e-8) with
+ *     learning rate lr; *loss (may be NULL) gets L before the update.
+ *   lbm_corrector_apply: rho, u of the domain's current level -> du -> lbm_apply_velocity_correction.
+ *   lbm_apply_velocity_correction: the post-collision populations of the previous level gain
+ *     f_eq(rho, u + du) - f_eq(rho, u) at every fluid cell (rho, u of the current level); du are
+ *     three planes on the dense box (host or device pointers); waits.
+ *   lbm_restrict: coarse rho, u (dense, device) = mean over the fluid children of each coarse
+ *     cell of the fine dense fields (fine extents even; fine_mask nonzero = fluid, device).
+ * All device pointers belong to the caller.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+typedef struct lbm_corrector lbm_corrector;
+int64_t lbm_corrector_num_params(void);
+lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz, double u_scale,
+                                double rho_scale, double du_scale, const float* params, lbm_alloc_fn alloc,
+                                lbm_free_fn release, void* alloc_ctx, void* cuda_stream, lbm_corrector** out);
+lbm_status lbm_corrector_get_params(lbm_corrector* c, float* params);
+lbm_status lbm_corrector_set_params(lbm_corrector* c, const float* params);
+lbm_status lbm_corrector_forward(lbm_corrector* c, const float* rho, const float* u, float* du);
+lbm_status lbm_corrector_gradients(lbm_corrector* c, const float* rho, const float* u, const float* u_target,
+                                   float* grad, double* loss);
+lbm_status lbm_corrector_train_step(lbm_corrector* c, const float* rho, const float* u, const float* u_target,
+                                    double lr, double* loss);
+lbm_status lbm_corrector_apply(lbm_corrector* c, lbm_domain* dom);
+void lbm_corrector_destroy(lbm_corrector* c);
+lbm_status lbm_apply_velocity_correction(lbm_domain* dom, const float* du, int32_t device_ptrs);
+lbm_status lbm_restrict(const float* fine_rho, const float* fine_u, const uint8_t* fine_mask, int32_t fnx,
+                        int32_t fny, int32_t fnz, float* coarse_rho, float* coarse_u, void* cuda_stream);
+
 /* Waits for all work enqueued on the domain. */
 lbm_status lbm_sync(lbm_domain* dom);
 

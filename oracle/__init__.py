@@ -44,6 +44,7 @@ def lib():
         L.oracle_waveform.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double]
         L.oracle_init_equilibrium.argtypes = [ctypes.c_void_p, dp, dp]
+        L.oracle_apply_velocity_correction.argtypes = [ctypes.c_void_p, dp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_get_threads.restype = ctypes.c_int
         L.oracle_stencil.argtypes = [ip, dp]
@@ -239,6 +240,13 @@ class Case:
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
         lib().oracle_init_equilibrium(self._h, rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+    def apply_velocity_correction(self, du):
+        """Post-collision populations of the previous level += f_eq(rho, u + du) - f_eq(rho, u)
+        at every fluid cell (rho, u of the current level), then re-streamed and re-closed;
+        du: (3, nz, ny, nx)."""
+        du = np.ascontiguousarray(du, dtype=np.float64).reshape(-1)
+        lib().oracle_apply_velocity_correction(self._h, du.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
     def get_f(self):
         out = np.zeros((self.nfluid, 27))

@@ -629,6 +629,36 @@ void oracle_init_equilibrium(oracle_case* C, const double* rho, const double* u)
     apply_open_boundaries(C, C->n);
 }
 
+/* Velocity correction of the learned coarse-grid corrector (not in the paper): at every fluid
+ * cell, with rho and u of level n (u with the half-force shift), the post-collision populations
+ * of level n-1 gain f_eq(rho, u + du) - f_eq(rho, u); level n is then streamed and closed again.
+ * du: three planes on the dense box. */
+void oracle_apply_velocity_correction(oracle_case* C, const double* du)
+{
+    int64_t nbox = (int64_t)C->nx * C->ny * C->nz;
+    double g[3];
+    gforce(C, C->n, g);
+    for (int64_t k = 0; k < C->nfluid; ++k) {
+        const double* f = C->f + k * NQ;
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < NQ; ++i) {
+            r += f[i];
+            for (int d = 0; d < 3; ++d) j[d] += cvel(i, d) * f[i];
+        }
+        int64_t b = C->cell[k];
+        double u0[3], u1[3], fa[NQ], fb[NQ];
+        for (int d = 0; d < 3; ++d) {
+            u0[d] = j[d] / r + 0.5 * g[d];
+            u1[d] = u0[d] + du[d * nbox + b];
+        }
+        oracle_feq_product(r, u1, fa);
+        oracle_feq_product(r, u0, fb);
+        for (int i = 0; i < NQ; ++i) C->fpost[k * NQ + i] += fa[i] - fb[i];
+    }
+    stream(C);
+    apply_open_boundaries(C, C->n);
+}
+
 /* rho and u (with the half-force shift at the current time level) on the dense box, x fastest;
  * solid cells get rho = 0, u = 0. */
 void oracle_macroscopic(const oracle_case* C, double* rho, double* u)

@@ -637,6 +637,70 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Velocity correction (learned corrector): the post-collision populations of the previous level
+// gain rho (prod psi(u + du) - prod psi(u)) at every fluid cell, rho and u those of the current
+// level.  The product difference is expanded, (a + da)(b + db)(c + dc) - abc =
+// da (b + db)(c + dc) + a db (c + dc) + a b dc, with dpsi(0) = -(2u + du) du and
+// dpsi(+-1) = (+-du + (2u + du) du)/2, so that no O(1) value is rounded against a small one.
+template <int ST, int SCHEME>
+__global__ void __launch_bounds__(256)
+    k_apply_du(DomainView v, void* pop, int parity_prev, const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,
+               const float* rho_in, const float* u_in, const float* du_in, int64_t n_box)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_fluid) return;
+    const int64_t b = fl_box[k];
+    const uint32_t slot = (uint32_t)fl_slot[k];
+    const float rho = rho_in[b];
+    float ps[3][3], dp[3][3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float u = u_in[ax * n_box + b], du = du_in[ax * n_box + b];
+        const float uu = u * u;
+        ps[ax][0] = 1.0f / 6.0f + 0.5f * (uu - u);
+        ps[ax][1] = 2.0f / 3.0f - uu;
+        ps[ax][2] = 1.0f / 6.0f + 0.5f * (uu + u);
+        const float s2 = (2.0f * u + du) * du;
+        dp[ax][0] = 0.5f * (s2 - du);
+        dp[ax][1] = -s2;
+        dp[ax][2] = 0.5f * (s2 + du);
+    }
+    float delta[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int ix = cx_of(i) + 1, iy = cy_of(i) + 1, iz = cz_of(i) + 1;
+        const float by = ps[1][iy] + dp[1][iy], bz = ps[2][iz] + dp[2][iz];
+        delta[i] = rho * (dp[0][ix] * by * bz + ps[0][ix] * dp[1][iy] * bz + ps[0][ix] * ps[1][iy] * dp[2][iz]);
+    }
+    const uint32_t n = (uint32_t)v.n_slots;
+    if (SCHEME == LBM_SCHEME_ESOTERIC) {
+        uint32_t cs[8];
+        corner_slots(v.nb8 + (slot / BRICK_CELLS) * 8, slot, cs);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t dir = parity_prev ? (uint32_t)i : (uint32_t)(Q - 1 - i);
+            const uint32_t off = dir * n + cs[corner_pos(i)];
+            Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
+        }
+        const uint32_t word = v.word[slot];
+        if (((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) {
+            const uint32_t rec = (uint32_t)v.aux[slot];
+            const uint32_t nbq = (uint32_t)v.n_bq;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t off = (uint32_t)i * nbq + rec;
+                Store<ST>::store(v.side, i, off, Store<ST>::load_rw(v.side, i, off) + delta[i]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t off = (uint32_t)i * n + slot;
+            Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
+        }
+    }
+}
+
 // FP64 diagnostics: per-block partial sums in a fixed order; one block then reduces the
 // partials in a fixed order (reproducible run to run).
 constexpr int DIAG_THREADS = 256;
@@ -778,6 +842,21 @@ cudaError_t launch_diagnostics(int scheme, const DomainView& v, const void* src,
     return cudaGetLastError();
 }
 
+template <int ST>
+cudaError_t launch_apply_du(int scheme, const DomainView& v, void* pop, int parity_prev, const int32_t* fl_slot,
+                           const int32_t* fl_box, int64_t n_fluid, const float* rho, const float* u, const float* du,
+                           int64_t n_box, cudaStream_t s)
+{
+    if (n_fluid == 0) return cudaSuccess;
+    if (scheme == LBM_SCHEME_ESOTERIC)
+        k_apply_du<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, pop, parity_prev, fl_slot, fl_box,
+                                                                               n_fluid, rho, u, du, n_box);
+    else
+        k_apply_du<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, pop, parity_prev, fl_slot, fl_box, n_fluid,
+                                                                         rho, u, du, n_box);
+    return cudaGetLastError();
+}
+
 template <int ST, int BRICKS, int MINB>
 cudaError_t launch_step_batch_t(const BatchEntry* ent, const int64_t* brick_start, int n_dom, int64_t total_bricks,
                                 const LevelArgs* args, int fast, cudaStream_t s)
@@ -808,7 +887,7 @@ template <int ST>
 const Launchers& make_launchers()
 {
     static const Launchers L = {&launch_step<ST>, &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
-                                &launch_diagnostics<ST>, &launch_step_batch<ST>};
+                                &launch_diagnostics<ST>, &launch_step_batch<ST>, &launch_apply_du<ST>};
     return L;
 }
 

@@ -674,6 +674,37 @@ lbm_status lbm_get_macroscopic(lbm_domain* D, float* rho, float* u, int32_t dens
     return LBM_OK;
 }
 
+lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t device_ptrs)
+{
+    g_last_error.clear();
+    if (!D || !du) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
+    const size_t bytes = sizeof(float) * (size_t)(device_ptrs ? 4 : 7) * (size_t)std::max<int64_t>(n_box, 1);
+    float* stage = static_cast<float*>(D->dev_alloc(bytes));
+    if (!stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+    float* rho = stage;
+    float* u = stage + n_box;
+    const float* dd = du;
+    cudaError_t e = cudaSuccess;
+    if (!device_ptrs) {
+        e = cudaMemcpyAsync(stage + 4 * n_box, du, sizeof(float) * 3 * n_box, cudaMemcpyHostToDevice, D->stream);
+        dd = stage + 4 * n_box;
+    }
+    const LevelArgs a = D->level_args(D->time);
+    const Launchers& L = launchers(D->params.storage);
+    if (e == cudaSuccess)
+        e = L.macroscopic(D->params.scheme, D->view, D->src(), a, D->d_fl_slot, D->d_fl_box, D->n_fluid, 1, rho, u,
+                          n_box, D->stream);
+    if (e == cudaSuccess)
+        e = L.apply_du(D->params.scheme, D->view, D->src(), (int)((D->time + 1) & 1), D->d_fl_slot, D->d_fl_box,
+                       D->n_fluid, rho, u, dd, n_box, D->stream);
+    cudaError_t e2 = cudaStreamSynchronize(D->stream);
+    if (e == cudaSuccess) e = e2;
+    D->dev_free(stage, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "velocity correction");
+    return LBM_OK;
+}
+
 lbm_status lbm_get_diagnostics(lbm_domain* D, lbm_diagnostics* out)
 {
     g_last_error.clear();

@@ -93,6 +93,10 @@ struct Launchers {
     // twist only: every domain of the batch one step; args[d] are domain d's level arguments
     cudaError_t (*step_batch)(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
                               int64_t total_bricks, const LevelArgs* args, int fast, cudaStream_t stream);
+    // learned-corrector velocity shift of the post-collision populations of the previous level
+    cudaError_t (*apply_du)(int scheme, const DomainView& v, void* pop, int parity_prev, const int32_t* fl_slot,
+                            const int32_t* fl_box, int64_t n_fluid, const float* rho, const float* u, const float* du,
+                            int64_t n_box, cudaStream_t stream);
 };
 const Launchers& launchers_fp32();
 const Launchers& launchers_fp16();

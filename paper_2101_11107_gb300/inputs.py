@@ -305,3 +305,18 @@ def taylor_green(nx: int, ny: int, nz: int, u0: float = 0.01):
     u[0] = ux[None]
     u[1] = uy[None]
     return rho, u
+
+
+# --------------------------------------------------------------------------------- corrector
+def corrector_init_params(seed: int):
+    """Seeded initial parameters of the 3-layer corrector network: weights (27, 16, 16) per
+    layer, He-normal with fan-in 27 x 16 (the last layer scaled by 0.1), biases zero; rounded
+    to FP32.  Returned as [W1, b1, W2, b2, W3, b3]."""
+    rng = np.random.default_rng(7_000_001 + seed)
+    std = np.sqrt(2.0 / (27 * 16))
+    ws = [rng.normal(0.0, std, (27, 16, 16)), rng.normal(0.0, std, (27, 16, 16)),
+          rng.normal(0.0, 0.1 * std, (27, 16, 16))]
+    out = []
+    for w in ws:
+        out += [w.astype(np.float32).astype(np.float64), np.zeros(16)]
+    return out

@@ -23,7 +23,10 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_step", "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
            "lbm_save_state", "lbm_load_state", "lbm_destroy", "lbm_last_error", "lbm_set_launch_config",
            "lbm_autotune", "lbm_get_diagnostics_noalloc", "lbm_batch_create", "lbm_batch_step",
-           "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_batch_destroy"]
+           "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_batch_destroy", "lbm_corrector_num_params",
+           "lbm_corrector_create", "lbm_corrector_get_params", "lbm_corrector_set_params", "lbm_corrector_forward",
+           "lbm_corrector_gradients", "lbm_corrector_train_step", "lbm_corrector_apply", "lbm_corrector_destroy",
+           "lbm_apply_velocity_correction", "lbm_restrict"]
 N_LAUNCH_CONFIGS = 5
 LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10"]
 SCHEME = {"ab": 0, "esoteric": 1}
@@ -102,6 +105,20 @@ def load_library(path: str = LIB_PATH):
     L.lbm_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
+    L.lbm_corrector_num_params.argtypes = []
+    L.lbm_corrector_num_params.restype = i64
+    L.lbm_corrector_create.argtypes = [vp, i32, i32, i32, dbl, dbl, dbl, vp, ALLOC_FN, FREE_FN, vp, vp,
+                                       ctypes.POINTER(vp)]
+    L.lbm_corrector_get_params.argtypes = [vp, vp]
+    L.lbm_corrector_set_params.argtypes = [vp, vp]
+    L.lbm_corrector_forward.argtypes = [vp, vp, vp, vp]
+    L.lbm_corrector_gradients.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    L.lbm_corrector_train_step.argtypes = [vp, vp, vp, vp, dbl, ctypes.POINTER(dbl)]
+    L.lbm_corrector_apply.argtypes = [vp, vp]
+    L.lbm_corrector_destroy.argtypes = [vp]
+    L.lbm_corrector_destroy.restype = None
+    L.lbm_apply_velocity_correction.argtypes = [vp, vp, i32]
+    L.lbm_restrict.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
@@ -294,11 +311,131 @@ class Domain:
             _check(st)
         return dg.as_dict()
 
+    def macroscopic_tensors(self):
+        """(rho, u) of the current level as dense CUDA float32 tensors (nz,ny,nx), (3,nz,ny,nx)."""
+        import torch
+        nz, ny, nx = self.shape
+        rho = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+        u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=self.device)
+        self.macroscopic_device(rho, u, dense=True)
+        return rho, u
+
+    def apply_velocity_correction(self, du):
+        """Post-collision populations of the previous level += f_eq(rho, u + du) - f_eq(rho, u);
+        du: (3, nz, ny, nx) numpy array or CUDA tensor."""
+        import torch
+        L = load_library()
+        if isinstance(du, torch.Tensor):
+            t = du.to(torch.float32).contiguous()
+            _check(L.lbm_apply_velocity_correction(self._h, ctypes.c_void_p(t.data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(du, dtype=np.float32)
+            _check(L.lbm_apply_velocity_correction(self._h, _ptr(a), 0))
+
     def save_state(self, path):
         _check(load_library().lbm_save_state(self._h, os.fsencode(path)))
 
     def load_state(self, path):
         _check(load_library().lbm_load_state(self._h, os.fsencode(path)))
+
+
+def flatten_params(params):
+    """[W1, b1, W2, b2, W3, b3] -> one FP32 vector in the C-ABI's order."""
+    return np.concatenate([np.asarray(p, dtype=np.float32).reshape(-1) for p in params])
+
+
+def unflatten_params(vec):
+    out, k = [], 0
+    for _ in range(3):
+        out.append(np.asarray(vec[k:k + 27 * 256], dtype=np.float64).reshape(27, 16, 16))
+        k += 27 * 256
+        out.append(np.asarray(vec[k:k + 16], dtype=np.float64))
+        k += 16
+    return out
+
+
+class Corrector:
+    """The learned coarse-grid corrector (lbm_corrector_* in include/lbm.h).  Fields are dense
+    CUDA float32 tensors on the coarse box: rho (nz,ny,nx), u (3,nz,ny,nx)."""
+
+    def __init__(self, mask, params, u_scale=0.05, rho_scale=0.01, du_scale=0.005, device=None, stream=None):
+        import torch
+        L = load_library()
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self.shape = mask.shape
+        nz, ny, nx = mask.shape
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        self.n_params = int(L.lbm_corrector_num_params())
+        vec = flatten_params(params) if isinstance(params, (list, tuple)) else np.asarray(params, np.float32)
+        assert vec.size == self.n_params
+        self._alloc = TorchAllocator(self.device)
+        h = ctypes.c_void_p()
+        _check(L.lbm_corrector_create(_ptr(mask), nx, ny, nz, float(u_scale), float(rho_scale), float(du_scale),
+                                      _ptr(vec), self._alloc.alloc_fn, self._alloc.free_fn, None,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def forward(self, rho, u):
+        import torch
+        du = torch.empty_like(u, dtype=torch.float32)
+        _check(load_library().lbm_corrector_forward(self._h, self._p(rho.contiguous()), self._p(u.contiguous()),
+                                                    self._p(du)))
+        return du
+
+    def gradients(self, rho, u, u_target):
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        _check(load_library().lbm_corrector_gradients(self._h, self._p(rho.contiguous()), self._p(u.contiguous()),
+                                                      self._p(u_target.contiguous()), _ptr(g), ctypes.byref(loss)))
+        return loss.value, unflatten_params(g)
+
+    def train_step(self, rho, u, u_target, lr):
+        loss = ctypes.c_double()
+        _check(load_library().lbm_corrector_train_step(self._h, self._p(rho.contiguous()), self._p(u.contiguous()),
+                                                       self._p(u_target.contiguous()), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def apply(self, domain):
+        _check(load_library().lbm_corrector_apply(self._h, domain._h))
+
+    def params(self):
+        vec = np.zeros(self.n_params, np.float32)
+        _check(load_library().lbm_corrector_get_params(self._h, _ptr(vec)))
+        return vec
+
+    def set_params(self, vec):
+        vec = np.ascontiguousarray(vec, dtype=np.float32)
+        _check(load_library().lbm_corrector_set_params(self._h, _ptr(vec)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().lbm_corrector_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def restrict(fine_rho, fine_u, fine_mask):
+    """Coarse (rho, u) = mean over the fluid children of each coarse cell (CUDA tensors)."""
+    import torch
+    nz, ny, nx = fine_rho.shape
+    crho = torch.empty((nz // 2, ny // 2, nx // 2), dtype=torch.float32, device=fine_rho.device)
+    cu = torch.empty((3, nz // 2, ny // 2, nx // 2), dtype=torch.float32, device=fine_rho.device)
+    m = fine_mask.to(torch.uint8).contiguous()
+    _check(load_library().lbm_restrict(ctypes.c_void_p(fine_rho.contiguous().data_ptr()),
+                                       ctypes.c_void_p(fine_u.contiguous().data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                                       nx, ny, nz, ctypes.c_void_p(crho.data_ptr()), ctypes.c_void_p(cu.data_ptr()),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return crho, cu
 
 
 class Batch:

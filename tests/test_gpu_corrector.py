@@ -1,0 +1,143 @@
+"""GPU parity of the learned corrector's kernels against the FP64 numpy oracle
+(oracle/corrector.py) and of the velocity-correction step against the C oracle.
+
+Tolerances: the network runs in BF16 (8 significant bits) with FP32 accumulation, so its output
+at fluid cells is held to 2e-2 relative L2 of the FP64 result; gradients (BF16 activations and
+output-gradients, FP32 accumulation) to cosine similarity >= 0.999 and relative L2 <= 3e-2 per
+parameter block.  Restriction and the velocity correction are FP32 and held to 1e-6 / 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import corrector as K
+from paper_2101_11107_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2101_11107_gb300 import lbm  # noqa: E402
+
+US, RS, DS = 0.05, 0.01, 0.005
+
+
+def _case(n=16, seed=0):
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(*(np.arange(n) + 0.5,) * 3, indexing="ij")
+    mask = (((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - 0.4 * n) ** 2) < (0.3 * n) ** 2).astype(np.uint8)
+    mask[:, :, : n // 4] = 0
+    rho = (1.0 + 0.01 * rng.normal(size=mask.shape)).astype(np.float32)
+    u = (0.03 * rng.normal(size=(3,) + mask.shape)).astype(np.float32)
+    ut = (u + 0.004 * rng.normal(size=u.shape)).astype(np.float32)
+    params = I.corrector_init_params(seed)
+    params[1] = (0.05 * rng.normal(size=16)).astype(np.float32).astype(np.float64)
+    params[3] = (0.05 * rng.normal(size=16)).astype(np.float32).astype(np.float64)
+    params[5] = (0.05 * rng.normal(size=16)).astype(np.float32).astype(np.float64)
+    return mask, rho, u, ut, params
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_forward_matches_oracle(seed):
+    mask, rho, u, ut, params = _case(16, seed)
+    net = lbm.Corrector(mask, params, US, RS, DS)
+    du = net.forward(_t(rho), _t(u)).cpu().numpy()
+    x0 = K.features(rho.astype(np.float64), u.astype(np.float64), mask, US, RS)
+    ref = K.correction(x0, mask, params, DS)
+    fl = mask > 0
+    assert _rel(du[:, fl], ref[:, fl]) < 2e-2
+    assert np.all(du[:, ~fl] == 0)
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_gradients_match_oracle(seed):
+    mask, rho, u, ut, params = _case(16, seed)
+    net = lbm.Corrector(mask, params, US, RS, DS)
+    loss, grads = net.gradients(_t(rho), _t(u), _t(ut))
+    x0 = K.features(rho.astype(np.float64), u.astype(np.float64), mask, US, RS)
+    target = (ut.astype(np.float64) - u) / DS
+    ref_loss, ref_grads = K.loss_and_grad(x0, target, mask, params)
+    assert abs(loss - ref_loss) < 2e-2 * ref_loss
+    for name, g, r in zip(["W1", "b1", "W2", "b2", "W3", "b3"], grads, ref_grads):
+        g, r = g.reshape(-1), r.reshape(-1)
+        cos = float(g @ r / (np.linalg.norm(g) * np.linalg.norm(r)))
+        assert cos >= 0.999, (name, cos)
+        assert _rel(g, r) <= 3e-2, (name, _rel(g, r))
+
+
+def test_training_reduces_loss():
+    """Adam on the GPU kernels fits a fixed synthetic correction (a smooth function of u):
+    the loss falls at least tenfold in 300 steps."""
+    mask, rho, u, _, params = _case(16, 5)
+    ut = u.copy()
+    ut[0] += 0.1 * u[1]
+    ut[2] -= 0.05 * u[0]
+    net = lbm.Corrector(mask, params, US, RS, DS)
+    tr, tu, tt = _t(rho), _t(u), _t(ut)
+    first = net.train_step(tr, tu, tt, 3e-3)
+    for _ in range(300):
+        last = net.train_step(tr, tu, tt, 3e-3)
+    assert last < first / 10.0, (first, last)
+
+
+def test_restriction_matches_oracle():
+    rng = np.random.default_rng(4)
+    fm = (rng.uniform(size=(8, 12, 16)) > 0.4).astype(np.uint8)
+    fr = (1 + 0.01 * rng.normal(size=fm.shape)).astype(np.float32)
+    fu = (0.02 * rng.normal(size=(3,) + fm.shape)).astype(np.float32)
+    cr, cu = lbm.restrict(_t(fr), _t(fu), _t(fm))
+    assert np.allclose(cr.cpu().numpy(), K.restrict(fr.astype(np.float64), fm), rtol=1e-6, atol=1e-7)
+    assert np.allclose(cu.cpu().numpy(), K.restrict(fu.astype(np.float64), fm), rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("scheme", ["esoteric", "ab"])
+def test_velocity_correction_matches_oracle(scheme):
+    """Aneurysm (Bouzidi walls, inlet, outlet): 57 steps, a smooth synthetic du applied to the
+    post-collision populations, 40 more steps; every cell against the oracle doing the same."""
+    g = I.aneurysm(8, edge=64, period=200.0, reynolds=30.0)
+    dom = lbm.Domain.from_geometry(g, scheme=scheme)
+    ref = oracle.Case(g.mask, periodic=g.periodic, links=g.links, inlet_center=g.inlet_center,
+                      inlet_radius=g.inlet_radius, tau=g.tau)
+    ref.set_waveform(*g.wave)
+    dom.step(57)
+    ref.step(57)
+    nz, ny, nx = g.mask.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    du = np.stack([0.002 * np.sin(x / 7.0), 0.001 * np.cos(y / 5.0), -0.0015 * np.sin(z / 9.0)])
+    du = du.astype(np.float32) * (g.mask > 0)
+    dom.apply_velocity_correction(du)
+    ref.apply_velocity_correction(du.astype(np.float64))
+    r0, u0 = dom.macroscopic()
+    rr0, ur0 = ref.macroscopic()
+    assert np.abs(u0 - ur0).max() / np.abs(ur0).max() <= 1e-5
+    dom.step(40)
+    ref.step(40)
+    r1, u1 = dom.macroscopic()
+    rr1, ur1 = ref.macroscopic()
+    assert np.abs(u1 - ur1).max() / np.abs(ur1).max() <= 1e-5
+    assert np.abs(r1 - rr1).max() <= 1e-5
+
+
+def test_apply_through_corrector():
+    """lbm_corrector_apply = export rho, u -> network -> velocity correction."""
+    g = I.aneurysm(9, edge=64, period=200.0, reynolds=30.0)
+    params = I.corrector_init_params(2)
+    a = lbm.Domain.from_geometry(g)
+    b = lbm.Domain.from_geometry(g)
+    a.step(30)
+    b.step(30)
+    net = lbm.Corrector(g.mask, params, US, RS, DS)
+    net.apply(a)
+    rho, u = b.macroscopic_tensors()
+    b.apply_velocity_correction(net.forward(rho, u))
+    assert np.array_equal(a.macroscopic()[1], b.macroscopic()[1])

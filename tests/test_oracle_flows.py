@@ -177,3 +177,22 @@ def test_translational_invariance():
     _, u4 = c4.macroscopic()
     for z in range(4):
         assert np.abs(u4[:, z] - u1[:, 0]).max() < 1e-18
+
+
+def test_velocity_correction_sets_velocity():
+    """Adding f_eq(rho, u + du) - f_eq(rho, u) to the post-collision populations and re-streaming
+    moves the velocity of an interior cell of a uniform periodic flow by exactly du (its
+    neighbours received the same shift), and keeps the mass."""
+    mask = np.ones((4, 4, 4), np.uint8)
+    c = oracle.Case(mask, periodic=(1, 1, 1), tau=0.7)
+    rho0 = np.ones(mask.shape)
+    u0 = np.zeros((3,) + mask.shape)
+    u0[0] = 0.01
+    c.init_equilibrium(rho0, u0)
+    r0, _ = c.macroscopic()
+    du = np.zeros((3,) + mask.shape)
+    du[1] = 0.003
+    c.apply_velocity_correction(du)
+    r1, u1 = c.macroscopic()
+    assert np.allclose(u1[0], 0.01, atol=1e-15) and np.allclose(u1[1], 0.003, atol=1e-15)
+    assert abs(r1.sum() - r0.sum()) < 1e-12
