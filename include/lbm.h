@@ -247,8 +247,12 @@ void lbm_batch_destroy(lbm_batch* batch);
  *   O  = conv3(relu(conv2(relu(conv1(X0)))));  du = du_scale * O[0:3] at fluid cells.
  * Parameters (FP32, lbm_corrector_num_params() of them): W1[27][16][16], b1[16], W2, b2, W3, b3
  * with W[o][out][in], offset o = (dx+1) + 3(dy+1) + 9(dz+1).
- *   lbm_corrector_create: mask[nx*ny*nz] (nonzero = fluid) of the coarse box (extents multiples
- *     of 4); the scales; initial params (copied).  Memory through the allocator callbacks.
+ *   lbm_corrector_create: mask[nx*ny*nz] (host; nonzero = fluid) of the coarse box (extents
+ *     multiples of 4): the network is evaluated on the tiles near its fluid (for training over
+ *     several geometries give the union of their masks); the scales; initial params (copied).
+ *     Memory through the allocator callbacks.
+ *   The calls below take a dense device cell mask (nonzero = fluid, inside the creation mask),
+ *   or NULL for the creation mask.
  *   lbm_corrector_forward: rho[n], u[3][n] dense device fields -> du[3][n] device.
  *   lbm_corrector_gradients: loss L = mean over fluid cells and components of
  *     (O[0:3] - (u_target - u)/du_scale)^2 and dL/dparams (host, FP32); waits.
@@ -269,11 +273,12 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
                                 lbm_free_fn release, void* alloc_ctx, void* cuda_stream, lbm_corrector** out);
 lbm_status lbm_corrector_get_params(lbm_corrector* c, float* params);
 lbm_status lbm_corrector_set_params(lbm_corrector* c, const float* params);
-lbm_status lbm_corrector_forward(lbm_corrector* c, const float* rho, const float* u, float* du);
-lbm_status lbm_corrector_gradients(lbm_corrector* c, const float* rho, const float* u, const float* u_target,
-                                   float* grad, double* loss);
-lbm_status lbm_corrector_train_step(lbm_corrector* c, const float* rho, const float* u, const float* u_target,
-                                    double lr, double* loss);
+lbm_status lbm_corrector_forward(lbm_corrector* c, const uint8_t* mask, const float* rho, const float* u,
+                                 float* du);
+lbm_status lbm_corrector_gradients(lbm_corrector* c, const uint8_t* mask, const float* rho, const float* u,
+                                   const float* u_target, float* grad, double* loss);
+lbm_status lbm_corrector_train_step(lbm_corrector* c, const uint8_t* mask, const float* rho, const float* u,
+                                    const float* u_target, double lr, double* loss);
 lbm_status lbm_corrector_apply(lbm_corrector* c, lbm_domain* dom);
 void lbm_corrector_destroy(lbm_corrector* c);
 lbm_status lbm_apply_velocity_correction(lbm_domain* dom, const float* du, int32_t device_ptrs);

@@ -1,0 +1,217 @@
+"""Coarse grid + learned corrector versus the fine grid, on seeded synthetic aneurysms.
+
+    python -m paper_2101_11107_gb300.corrector_study --out results.json            # full study
+    python -m paper_2101_11107_gb300.corrector_study --small --out small.json      # quick check
+
+Full study: fine 256^3 (tau from Re 300), coarse 128^3 with acoustic scaling (half the steps,
+tau_c - 1/2 = (tau_f - 1/2)/2, the same lattice velocity and waveform over half the period:
+Sec. 2.2.3 and 3.4 of the paper, 0.506 -> 0.503).  Training pairs come from the solver itself:
+coarse states and the fine states restricted onto the coarse grid at the same physical time,
+sampled in the last period of 32 seeded geometries; the corrector (3 conv layers, BF16 tensor
+cores) is trained on the GPU and applied every 50 coarse steps.  Evaluation on 8 held-out
+geometries: relative L2 error of u against the restricted fine run over the coarse fluid cells
+at 10 phases of the last cycle, the similarity index of the paper's Sec. 3.4 (read with the
+factor 1/2 that bounds it by 1), and CUDA-event wall times of the fine, coarse and
+coarse + corrector runs.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures
+import json
+import multiprocessing
+import time
+
+import numpy as np
+
+U_SCALE, RHO_SCALE, DU_SCALE = 0.05, 0.01, 0.005
+
+
+def _geometry_pair(args):
+    from . import inputs as I
+
+    seed, fine_edge, period_f, reynolds = args
+    gf = I.aneurysm(seed, edge=fine_edge, period=period_f, wave_seed=seed, reynolds=reynolds)
+    gc = I.aneurysm(seed, edge=fine_edge // 2, period=period_f / 2, wave_seed=seed, reynolds=reynolds)
+    return seed, gf, gc
+
+
+def geometry_pairs(seeds, fine_edge, period_f, reynolds, workers):
+    """Generated on the host in parallel (spawned workers: no CUDA in them)."""
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+        out = list(ex.map(_geometry_pair, [(s, fine_edge, period_f, reynolds) for s in seeds]))
+    return {s: (gf, gc) for s, gf, gc in out}
+
+
+def similarity_index(u_hr, u_lr, mask):
+    """Mean over fluid cells of 1/2 (1 + cos) (1 - | |u_hr|/max|u_hr| - |u_lr|/max|u_lr| |)."""
+    fl = mask > 0
+    a, b = u_hr[:, fl], u_lr[:, fl]
+    na, nb = np.linalg.norm(a, axis=0), np.linalg.norm(b, axis=0)
+    cos = (a * b).sum(0) / np.maximum(na * nb, 1e-30)
+    mag = 1.0 - np.abs(na / max(na.max(), 1e-30) - nb / max(nb.max(), 1e-30))
+    return float(np.mean(0.5 * (1.0 + cos) * mag))
+
+
+def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples_per_period, train_steps, lr,
+        apply_every, workers, log):
+    import torch
+
+    from . import inputs as I
+    from . import lbm
+
+    t0 = time.time()
+    pairs = geometry_pairs(list(train_seeds) + list(test_seeds), fine_edge, period_f, reynolds, workers)
+    log(f"geometries: {len(pairs)} pairs in {time.time() - t0:.1f} s")
+    torch.cuda.set_device(0)
+    period_c = period_f // 2
+    n_c = periods * period_c
+    phase_step = period_c // samples_per_period
+    sample_times = [n_c - period_c + k * phase_step for k in range(1, samples_per_period + 1)]
+    assert all(t % apply_every == 0 for t in sample_times)
+
+    def tensors_mask(g):
+        return torch.from_numpy(np.ascontiguousarray(g.mask > 0).astype(np.uint8)).cuda()
+
+    def simulate(gf, gc, corrector=None, sample=True):
+        """Fine, coarse (and optionally corrected coarse) runs over n_c coarse steps; returns the
+        samples at `sample_times` as dicts of CUDA tensors."""
+        fine = lbm.Domain.from_geometry(gf)
+        coarse = lbm.Domain.from_geometry(gc)
+        bf = lbm.Batch([fine], graph_steps=2 * apply_every)
+        bc = lbm.Batch([coarse], graph_steps=apply_every)
+        fmask = tensors_mask(gf)
+        out = []
+        for t in range(apply_every, n_c + 1, apply_every):
+            bf.step(2 * apply_every)
+            bc.step(apply_every)
+            if corrector is not None:
+                corrector.apply(coarse)
+            if sample and t in sample_times:
+                fr, fu = fine.macroscopic_tensors()
+                cr, cu = lbm.restrict(fr, fu, fmask)
+                rho, u = coarse.macroscopic_tensors()
+                out.append({"t": t, "rho": rho, "u": u, "u_fine": cu, "rho_fine": cr})
+        bf.close()
+        bc.close()
+        for d in (fine, coarse):
+            if d.diagnostics(raise_unstable=False)["n_nonfinite"]:
+                raise RuntimeError("the flow went unstable")
+        return out
+
+    # ---------------------------------------------------------------- training data
+    union = np.zeros(pairs[train_seeds[0]][1].mask.shape, bool)
+    for s in pairs:
+        union |= pairs[s][1].mask > 0
+    data = []
+    t1 = time.time()
+    for s in train_seeds:
+        gf, gc = pairs[s]
+        m = tensors_mask(gc)
+        for smp in simulate(gf, gc):
+            data.append((m, smp["rho"], smp["u"], smp["u_fine"]))
+    torch.cuda.synchronize()
+    log(f"training data: {len(data)} samples from {len(train_seeds)} geometries in {time.time() - t1:.1f} s")
+
+    # ---------------------------------------------------------------- training
+    net = lbm.Corrector(union.astype(np.uint8), I.corrector_init_params(0), U_SCALE, RHO_SCALE, DU_SCALE)
+    rng = np.random.default_rng(0)
+    losses = []
+    torch.cuda.synchronize()
+    t2 = time.time()
+    for k in range(train_steps):
+        m, rho, u, ut = data[rng.integers(len(data))]
+        step_lr = lr if k < 0.7 * train_steps else lr * 0.2
+        losses.append(net.train_step(rho, u, ut, step_lr, mask=m))
+    torch.cuda.synchronize()
+    train_s = time.time() - t2
+    log(f"training: {train_steps} steps in {train_s:.1f} s, loss {np.mean(losses[:50]):.4f} -> "
+        f"{np.mean(losses[-50:]):.4f}")
+
+    # ---------------------------------------------------------------- evaluation
+    results = []
+    for s in test_seeds:
+        gf, gc = pairs[s]
+        cm = gc.mask
+        plain = simulate(gf, gc)
+        corr = simulate(gf, gc, corrector=net)
+        e_plain, e_corr, si_plain, si_corr = [], [], [], []
+        for a, b in zip(plain, corr):
+            uf = a["u_fine"].cpu().numpy()
+            up = a["u"].cpu().numpy()
+            uc = b["u"].cpu().numpy()
+            fl = cm > 0
+            e_plain.append(float(np.linalg.norm((up - uf)[:, fl]) / np.linalg.norm(uf[:, fl])))
+            e_corr.append(float(np.linalg.norm((uc - uf)[:, fl]) / np.linalg.norm(uf[:, fl])))
+            si_plain.append(similarity_index(uf, up, cm))
+            si_corr.append(similarity_index(uf, uc, cm))
+        # wall times, no sampling inside
+        times = {}
+        for name in ("fine", "coarse", "coarse+corrector"):
+            g = gf if name == "fine" else gc
+            dom = lbm.Domain.from_geometry(g)
+            steps = 2 * n_c if name == "fine" else n_c
+            chunk = 2 * apply_every if name == "fine" else apply_every
+            b = lbm.Batch([dom], graph_steps=chunk)
+            b.step(chunk)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(chunk, steps + 1, chunk):
+                b.step(chunk)
+                if name == "coarse+corrector":
+                    net.apply(dom)
+            ev1.record()
+            torch.cuda.synchronize()
+            times[name] = ev0.elapsed_time(ev1) / 1e3
+            b.close()
+        r = {"seed": int(s), "fine_fluid": int(gf.nfluid), "coarse_fluid": int(gc.nfluid), "tau_fine": gf.tau,
+             "tau_coarse": gc.tau, "err_plain": float(np.mean(e_plain)), "err_corrected": float(np.mean(e_corr)),
+             "si_plain": float(np.mean(si_plain)), "si_corrected": float(np.mean(si_corr)),
+             "wall_s": times}
+        log(json.dumps(r))
+        results.append(r)
+    summary = {
+        "reynolds": reynolds, "fine_edge": fine_edge, "coarse_edge": fine_edge // 2, "period_fine": period_f, "periods": periods,
+        "train_seeds": list(map(int, train_seeds)), "test_seeds": list(map(int, test_seeds)),
+        "samples": len(data), "train_steps": train_steps, "train_s": train_s,
+        "loss_first50": float(np.mean(losses[:50])), "loss_last50": float(np.mean(losses[-50:])),
+        "apply_every": apply_every,
+        "err_plain_mean": float(np.mean([r["err_plain"] for r in results])),
+        "err_corrected_mean": float(np.mean([r["err_corrected"] for r in results])),
+        "si_plain_mean": float(np.mean([r["si_plain"] for r in results])),
+        "si_corrected_mean": float(np.mean([r["si_corrected"] for r in results])),
+        "wall_fine_s": float(np.mean([r["wall_s"]["fine"] for r in results])),
+        "wall_coarse_s": float(np.mean([r["wall_s"]["coarse"] for r in results])),
+        "wall_coarse_corrector_s": float(np.mean([r["wall_s"]["coarse+corrector"] for r in results])),
+        "per_geometry": results,
+    }
+    return summary, net
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--small", action="store_true")
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--weights", default=None)
+    ap.add_argument("--workers", type=int, default=16)
+    a = ap.parse_args(argv)
+    if a.small:
+        cfg = dict(fine_edge=128, period_f=800, reynolds=60.0, train_seeds=list(range(100, 106)),
+                   test_seeds=[200, 201], periods=3, samples_per_period=4, train_steps=600, lr=2e-3, apply_every=50)
+    else:
+        cfg = dict(fine_edge=256, period_f=4000, reynolds=300.0, train_seeds=list(range(100, 132)),
+                   test_seeds=list(range(200, 208)), periods=3, samples_per_period=10, train_steps=4000, lr=1e-3,
+                   apply_every=50)
+    summary, net = run(workers=a.workers, log=lambda m: print(m, flush=True), **cfg)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(summary, f, indent=1)
+    if a.weights:
+        np.save(a.weights, net.params())
+    print(json.dumps({k: v for k, v in summary.items() if k != "per_geometry"}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -248,14 +248,32 @@ __global__ void k_output(const float* __restrict__ o4, const uint8_t* __restrict
 
 // Loss = mean over fluid cells and components of (O - T)^2, T = (u_target - u) / du_scale;
 // dO = 2 (O - T) / N at fluid cells (BF16, padded, channels 0..2).
+__global__ void k_count(const uint8_t* __restrict__ mask, int64_t n, unsigned long long* __restrict__ count)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int ballot = __ballot_sync(0xffffffffu, c < n && mask[c] != 0);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(count, (unsigned long long)__popc(ballot));
+}
+
 __global__ void k_loss(const float* __restrict__ o4, const float* __restrict__ u, const float* __restrict__ ut,
-                       const uint8_t* __restrict__ mask, Box b, float inv_du, float two_over_n,
+                       const uint8_t* __restrict__ mask, Box b, float inv_du, const unsigned long long* __restrict__ count,
                        __nv_bfloat16* __restrict__ dO, double* __restrict__ loss)
 {
     __shared__ double sh[8];
+    const float two_over_n = *count ? 2.0f / (3.0f * (float)*count) : 0.0f;
     const int64_t n = (int64_t)b.nx * b.ny * b.nz;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double part = 0.0;
+    if (c < n) {
+        // zero the output gradient of every cell, so that a mask differing from the previous
+        // call's leaves no stale values behind
+        const int x = (int)(c % b.nx), y = (int)((c / b.nx) % b.ny), z = (int)(c / ((int64_t)b.nx * b.ny));
+        __nv_bfloat16* d = dO + pidx(b, x, y, z) * CH;
+        const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+        d[0] = zero;
+        d[1] = zero;
+        d[2] = zero;
+    }
     if (c < n && mask[c]) {
         const int x = (int)(c % b.nx), y = (int)((c / b.nx) % b.ny), z = (int)(c / ((int64_t)b.nx * b.ny));
         __nv_bfloat16* d = dO + pidx(b, x, y, z) * CH;
@@ -361,6 +379,7 @@ struct lbm_corrector {
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *wb = nullptr, *wt = nullptr;
     double* loss = nullptr;
+    unsigned long long* count = nullptr;
     int64_t adam_t = 0;
 
     void* dev(size_t bytes)
@@ -394,9 +413,10 @@ struct lbm_corrector {
         else k_conv<false><<<(int)n_tiles, 128, 0, stream>>>(in, w, bias, relu, gate, out, tiles, box);
         return cudaGetLastError();
     }
-    cudaError_t forward(const float* r, const float* uu)
+    cudaError_t forward(const uint8_t* cmask, const float* r, const float* uu)
     {
-        k_features<<<blocks(n_cells, 256), 256, 0, stream>>>(r, uu, mask, box, 1.0f / u_scale, 1.0f / rho_scale, x0);
+        k_features<<<blocks(n_cells, 256), 256, 0, stream>>>(r, uu, cmask ? cmask : mask, box, 1.0f / u_scale,
+                                                             1.0f / rho_scale, x0);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = conv(x0, wb, bmaster(0), 1, nullptr, y1, false);
         if (e == cudaSuccess) e = conv(y1, wb + NW, bmaster(1), 1, nullptr, y2, false);
@@ -404,13 +424,15 @@ struct lbm_corrector {
         return e;
     }
     // loss and gradients into `grad` (FP32, parameter layout), loss into `loss`
-    cudaError_t backward(const float* uu, const float* ut)
+    cudaError_t backward(const uint8_t* cmask, const float* uu, const float* ut)
     {
+        const uint8_t* mk = cmask ? cmask : mask;
         cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * NP, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
-        const float two_over_n = n_fluid ? 2.0f / (3.0f * (float)n_fluid) : 0.0f;
-        k_loss<<<blocks(n_cells, 256), 256, 0, stream>>>(o4, uu, ut, mask, box, 1.0f / du_scale, two_over_n, dO, loss);
+        k_count<<<blocks(n_cells, 256), 256, 0, stream>>>(mk, n_cells, count);
+        k_loss<<<blocks(n_cells, 256), 256, 0, stream>>>(o4, uu, ut, mk, box, 1.0f / du_scale, count, dO, loss);
         e = cudaGetLastError();
         const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_tiles, 1), 304);
         if (e == cudaSuccess && n_tiles)
@@ -512,6 +534,7 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
     K->wb = static_cast<__nv_bfloat16*>(D(sizeof(__nv_bfloat16) * 3 * NW));
     K->wt = static_cast<__nv_bfloat16*>(D(sizeof(__nv_bfloat16) * 3 * NW));
     K->loss = static_cast<double*>(D(sizeof(double)));
+    K->count = static_cast<unsigned long long*>(D(sizeof(unsigned long long)));
     if (!ok) {
         K->release_all();
         delete K;
@@ -559,40 +582,43 @@ lbm_status lbm_corrector_set_params(lbm_corrector* K, const float* params)
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_forward(lbm_corrector* K, const float* rho, const float* u, float* du)
+lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const float* rho, const float* u, float* du)
 {
     if (!K || !rho || !u || !du) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
-    cudaError_t e = K->forward(rho, u);
+    cudaError_t e = K->forward(mask, rho, u);
     if (e == cudaSuccess) {
-        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, K->mask, K->n_cells, K->du_scale, du);
+        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, mask ? mask : K->mask, K->n_cells, K->du_scale,
+                                                                 du);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector forward: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_gradients(lbm_corrector* K, const float* rho, const float* u, const float* u_target,
-                                   float* grad, double* loss)
+lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const float* rho, const float* u,
+                                   const float* u_target, float* grad, double* loss)
 {
     if (!K || !rho || !u || !u_target || !grad || !loss) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
-    cudaError_t e = K->forward(rho, u);
-    if (e == cudaSuccess) e = K->backward(u, u_target);
+    cudaError_t e = K->forward(mask, rho, u);
+    if (e == cudaSuccess) e = K->backward(mask, u, u_target);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, K->grad, sizeof(float) * NP, cudaMemcpyDeviceToHost, K->stream);
     double l = 0.0;
+    unsigned long long cnt = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, K->loss, sizeof(double), cudaMemcpyDeviceToHost, K->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, K->count, sizeof(cnt), cudaMemcpyDeviceToHost, K->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(K->stream);
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector gradients: ") + cudaGetErrorString(e));
-    *loss = K->n_fluid ? l / (3.0 * (double)K->n_fluid) : 0.0;
+    *loss = cnt ? l / (3.0 * (double)cnt) : 0.0;
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_train_step(lbm_corrector* K, const float* rho, const float* u, const float* u_target,
-                                    double lr, double* loss)
+lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const float* rho, const float* u,
+                                    const float* u_target, double lr, double* loss)
 {
     if (!K || !rho || !u || !u_target) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     if (!(lr > 0.0)) return nn_fail(LBM_ERR_INVALID_ARG, "lr must be > 0");
-    cudaError_t e = K->forward(rho, u);
-    if (e == cudaSuccess) e = K->backward(u, u_target);
+    cudaError_t e = K->forward(mask, rho, u);
+    if (e == cudaSuccess) e = K->backward(mask, u, u_target);
     K->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float bc1 = 1.0f - std::pow(b1, (float)K->adam_t), bc2 = 1.0f - std::pow(b2, (float)K->adam_t);
@@ -603,10 +629,12 @@ lbm_status lbm_corrector_train_step(lbm_corrector* K, const float* rho, const fl
     }
     if (e == cudaSuccess) e = K->prepare();
     double l = 0.0;
+    unsigned long long cnt = 0;
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(&l, K->loss, sizeof(double), cudaMemcpyDeviceToHost, K->stream);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(&cnt, K->count, sizeof(cnt), cudaMemcpyDeviceToHost, K->stream);
     if (e == cudaSuccess && loss) e = cudaStreamSynchronize(K->stream);
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector train step: ") + cudaGetErrorString(e));
-    if (loss) *loss = K->n_fluid ? l / (3.0 * (double)K->n_fluid) : 0.0;
+    if (loss) *loss = cnt ? l / (3.0 * (double)cnt) : 0.0;
     return LBM_OK;
 }
 
@@ -619,7 +647,7 @@ lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom)
         return nn_fail(LBM_ERR_INVALID_ARG, "the domain's box differs from the corrector's");
     lbm_status s = lbm_get_macroscopic(dom, K->rho, K->u, 1, 1);
     if (s) return s;
-    s = lbm_corrector_forward(K, K->rho, K->u, K->du);
+    s = lbm_corrector_forward(K, nullptr, K->rho, K->u, K->du);
     if (s) return s;
     return lbm_apply_velocity_correction(dom, K->du, 1);
 }
