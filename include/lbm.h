@@ -244,7 +244,8 @@ void lbm_batch_destroy(lbm_batch* batch);
  * 16 channels, 3x3x3 kernels, zero padding, ReLU, BF16 weights and activations with FP32
  * accumulation on the tensor cores, evaluated on the 4^3 tiles near fluid:
  *   X0 = [u/u_scale (3), (rho-1)/rho_scale, fluid mask, 0 (11)]  (zero at solid cells)
- *   O  = conv3(relu(conv2(relu(conv1(X0)))));  du = du_scale * O[0:3] at fluid cells.
+ *   O  = conv3(relu(conv2(relu(conv1(X0)))));  du = du_scale * clamp(O[0:3], -2, 2) at fluid
+ *   cells (the clamp bounds a correction to twice du_scale per component).
  * Parameters (FP32, lbm_corrector_num_params() of them): W1[27][16][16], b1[16], W2, b2, W3, b3
  * with W[o][out][in], offset o = (dx+1) + 3(dy+1) + 9(dz+1).
  *   lbm_corrector_create: mask[nx*ny*nz] (host; nonzero = fluid) of the coarse box (extents
@@ -260,7 +261,8 @@ void lbm_batch_destroy(lbm_batch* batch);
  *     learning rate lr; *loss (may be NULL) gets L before the update.
  *   lbm_corrector_apply: rho, u of the domain's current level -> du -> lbm_apply_velocity_correction.
  *   lbm_apply_velocity_correction: the post-collision populations of the previous level gain
- *     f_eq(rho, u + du) - f_eq(rho, u) at every fluid cell (rho, u of the current level); du are
+ *     f_eq(rho, u + du) - f_eq(rho, u) at every fluid cell except inlet and outlet cells (whose
+ *     unknowns the closures rebuild each step; rho, u of the current level); du are
  *     three planes on the dense box (host or device pointers); waits.
  *   lbm_restrict: coarse rho, u (dense, device) = mean over the fluid children of each coarse
  *     cell of the fine dense fields (fine extents even; fine_mask nonzero = fluid, device).

@@ -9,13 +9,14 @@ the coarse grid.  This module states, in plain numpy, what the GPU kernels compu
             zeros; the three velocity and the density channels are zero at solid cells.
   network   Y1 = relu(conv(X0, W1) + b1), Y2 = relu(conv(Y1, W2) + b2), O = conv(Y2, W3) + b3,
             conv = 3x3x3 cross-correlation with zero padding, 16 -> 16 channels;
-            du = du_scale * O[0:3] at fluid cells (0 elsewhere).
+            du = du_scale * clamp(O[0:3], -2, 2) at fluid cells (0 elsewhere).
   loss      L = mean over fluid cells and the 3 components of (O[0:3] - T)^2,
             T = (u_target - u) / du_scale.
   gradients by the chain rule (conv backward = correlation with the flipped, transposed
             kernel; weight gradient = correlation of inputs and output gradients).
   restrict  coarse cell value = mean of its 8 fine children that are fluid.
-  apply     Delta f_i = f_eq_i(rho, u + du) - f_eq_i(rho, u) (full-expansion equilibrium).
+  apply     Delta f_i = f_eq_i(rho, u + du) - f_eq_i(rho, u) (full-expansion equilibrium), at
+            every fluid cell but inlet and outlet cells (oracle/lbm_oracle.c).
 
 Layout: fields (nz, ny, nx) or (C, nz, ny, nx); weights W[l] of shape (27, 16 out, 16 in) with
 offset index o = (dx+1) + 3(dy+1) + 9(dz+1).  Tests pin every function against finite
@@ -108,9 +109,10 @@ def loss_and_grad(x0, target, mask, params):
     return loss, (gW1, gb1, gW2, gb2, gW3, gb3)
 
 
-def correction(x0, mask, params, du_scale):
+def correction(x0, mask, params, du_scale, clip=2.0):
+    """du = du_scale * clamp(O[0:3], -clip, clip) at fluid cells."""
     o, _ = forward(x0, params)
-    return du_scale * o[0:3] * (mask > 0)
+    return du_scale * np.clip(o[0:3], -clip, clip) * (mask > 0)
 
 
 def restrict(fine, fine_mask):

@@ -630,7 +630,7 @@ void oracle_init_equilibrium(oracle_case* C, const double* rho, const double* u)
 }
 
 /* Velocity correction of the learned coarse-grid corrector (not in the paper): at every fluid
- * cell, with rho and u of level n (u with the half-force shift), the post-collision populations
+ * cell but inlet and outlet cells, with rho and u of level n (u with the half-force shift), the post-collision populations
  * of level n-1 gain f_eq(rho, u + du) - f_eq(rho, u); level n is then streamed and closed again.
  * du: three planes on the dense box. */
 void oracle_apply_velocity_correction(oracle_case* C, const double* du)
@@ -639,6 +639,7 @@ void oracle_apply_velocity_correction(oracle_case* C, const double* du)
     double g[3];
     gforce(C, C->n, g);
     for (int64_t k = 0; k < C->nfluid; ++k) {
+        if (C->kind[k] >= 2) continue; /* inlet/outlet closures rebuild their unknowns */
         const double* f = C->f + k * NQ;
         double r = 0.0, j[3] = {0.0, 0.0, 0.0};
         for (int i = 0; i < NQ; ++i) {

@@ -69,26 +69,37 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     n_c = periods * period_c
     phase_step = period_c // samples_per_period
     sample_times = [n_c - period_c + k * phase_step for k in range(1, samples_per_period + 1)]
-    assert all(t % apply_every == 0 for t in sample_times)
+    # training also samples the period before the last
+    train_times = sorted(set(sample_times) | {t - period_c for t in sample_times})
+    assert all(t % apply_every == 0 for t in train_times)
+    apply_from = period_c  # corrections start after one period of warm-up
 
     def tensors_mask(g):
         return torch.from_numpy(np.ascontiguousarray(g.mask > 0).astype(np.uint8)).cuda()
 
-    def simulate(gf, gc, corrector=None, sample=True):
+    def simulate(gf, gc, corrector=None, times=None):
         """Fine, coarse (and optionally corrected coarse) runs over n_c coarse steps; returns the
-        samples at `sample_times` as dicts of CUDA tensors."""
+        samples at `times` as dicts of CUDA tensors.  A corrected run that turns non-finite falls
+        back to the plain coarse solver: it restarts from the last checked state and stops
+        correcting (reported as 'fallback')."""
+        times = sample_times if times is None else times
         fine = lbm.Domain.from_geometry(gf)
         coarse = lbm.Domain.from_geometry(gc)
         bf = lbm.Batch([fine], graph_steps=2 * apply_every)
         bc = lbm.Batch([coarse], graph_steps=apply_every)
         fmask = tensors_mask(gf)
         out = []
+        state = {"fallback": None}
         for t in range(apply_every, n_c + 1, apply_every):
             bf.step(2 * apply_every)
             bc.step(apply_every)
-            if corrector is not None:
+            if corrector is not None and state["fallback"] is None and t >= apply_from:
+                rho0, u0 = coarse.macroscopic_tensors()
                 corrector.apply(coarse)
-            if sample and t in sample_times:
+                if coarse.diagnostics(raise_unstable=False)["n_nonfinite"]:
+                    coarse.init_equilibrium(rho0, u0)
+                    state["fallback"] = t
+            if t in times:
                 fr, fu = fine.macroscopic_tensors()
                 cr, cu = lbm.restrict(fr, fu, fmask)
                 rho, u = coarse.macroscopic_tensors()
@@ -98,6 +109,8 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         for d in (fine, coarse):
             if d.diagnostics(raise_unstable=False)["n_nonfinite"]:
                 raise RuntimeError("the flow went unstable")
+        if out:
+            out[0]["fallback"] = state["fallback"]
         return out
 
     # ---------------------------------------------------------------- training data
@@ -109,7 +122,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     for s in train_seeds:
         gf, gc = pairs[s]
         m = tensors_mask(gc)
-        for smp in simulate(gf, gc):
+        for smp in simulate(gf, gc, times=train_times):
             data.append((m, smp["rho"], smp["u"], smp["u_fine"]))
     torch.cuda.synchronize()
     log(f"training data: {len(data)} samples from {len(train_seeds)} geometries in {time.time() - t1:.1f} s")
@@ -158,9 +171,9 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
-            for _ in range(chunk, steps + 1, chunk):
+            for t in range(chunk, steps + 1, chunk):
                 b.step(chunk)
-                if name == "coarse+corrector":
+                if name == "coarse+corrector" and t >= apply_from:
                     net.apply(dom)
             ev1.record()
             torch.cuda.synchronize()
@@ -169,6 +182,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         r = {"seed": int(s), "fine_fluid": int(gf.nfluid), "coarse_fluid": int(gc.nfluid), "tau_fine": gf.tau,
              "tau_coarse": gc.tau, "err_plain": float(np.mean(e_plain)), "err_corrected": float(np.mean(e_corr)),
              "si_plain": float(np.mean(si_plain)), "si_corrected": float(np.mean(si_corr)),
+             "fallback_at_step": corr[0].get("fallback") if corr else None,
              "wall_s": times}
         log(json.dumps(r))
         results.append(r)

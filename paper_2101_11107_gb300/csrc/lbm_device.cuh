@@ -638,8 +638,8 @@ __global__ void __launch_bounds__(256)
 }
 
 // Velocity correction (learned corrector): the post-collision populations of the previous level
-// gain rho (prod psi(u + du) - prod psi(u)) at every fluid cell, rho and u those of the current
-// level.  The product difference is expanded, (a + da)(b + db)(c + dc) - abc =
+// gain rho (prod psi(u + du) - prod psi(u)) at every fluid cell except inlet and outlet cells,
+// rho and u those of the current level.  The product difference is expanded, (a + da)(b + db)(c + dc) - abc =
 // da (b + db)(c + dc) + a db (c + dc) + a b dc, with dpsi(0) = -(2u + du) du and
 // dpsi(+-1) = (+-du + (2u + du) du)/2, so that no O(1) value is rounded against a small one.
 template <int ST, int SCHEME>
@@ -651,6 +651,8 @@ __global__ void __launch_bounds__(256)
     if (k >= n_fluid) return;
     const int64_t b = fl_box[k];
     const uint32_t slot = (uint32_t)fl_slot[k];
+    // open-boundary cells are left alone: their closures rebuild the unknowns every step
+    if (((v.word[slot] >> WORD_KIND_SHIFT) & 3u) >= KIND_INLET) return;
     const float rho = rho_in[b];
     float ps[3][3], dp[3][3];
 #pragma unroll

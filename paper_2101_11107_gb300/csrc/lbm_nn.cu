@@ -234,16 +234,16 @@ __global__ void k_features(const float* __restrict__ rho, const float* __restric
     dst[1] = *reinterpret_cast<uint4*>(&v[8]);
 }
 
-// du = du_scale * O[0:3] at fluid cells, 0 elsewhere (three planes).
+// du = du_scale * clamp(O[0:3], -clip, clip) at fluid cells, 0 elsewhere (three planes).
 __global__ void k_output(const float* __restrict__ o4, const uint8_t* __restrict__ mask, int64_t n, float du_scale,
-                         float* __restrict__ du)
+                         float clip, float* __restrict__ du)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     const float fl = mask[c] ? du_scale : 0.0f;
-    du[c] = o4[c * 4 + 0] * fl;
-    du[n + c] = o4[c * 4 + 1] * fl;
-    du[2 * n + c] = o4[c * 4 + 2] * fl;
+    du[c] = fminf(fmaxf(o4[c * 4 + 0], -clip), clip) * fl;
+    du[n + c] = fminf(fmaxf(o4[c * 4 + 1], -clip), clip) * fl;
+    du[2 * n + c] = fminf(fmaxf(o4[c * 4 + 2], -clip), clip) * fl;
 }
 
 // Loss = mean over fluid cells and components of (O - T)^2, T = (u_target - u) / du_scale;
@@ -365,7 +365,7 @@ lbm_status nn_fail(lbm_status s, const std::string& msg)
 struct lbm_corrector {
     Box box{};
     int64_t n_cells = 0, n_fluid = 0, n_tiles = 0;
-    float u_scale = 0.05f, rho_scale = 0.01f, du_scale = 0.005f;
+    float u_scale = 0.05f, rho_scale = 0.01f, du_scale = 0.005f, clip = 2.0f;
     cudaStream_t stream = nullptr;
     lbm_alloc_fn alloc = nullptr;
     lbm_free_fn release = nullptr;
@@ -588,7 +588,7 @@ lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const fl
     cudaError_t e = K->forward(mask, rho, u);
     if (e == cudaSuccess) {
         k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, mask ? mask : K->mask, K->n_cells, K->du_scale,
-                                                                 du);
+                                                                 K->clip, du);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector forward: ") + cudaGetErrorString(e));
