@@ -4,8 +4,9 @@
 Tolerances: the network runs in BF16 (8 significant bits) with FP32 accumulation, so its output
 at fluid cells is held to 2e-2 relative L2 of the FP64 result.  Gradients (BF16 activations and
 output-gradients, FP32 accumulation) pick up one BF16 rounding of the back-propagated gradient
-per layer they pass (dO, then dz2, then dz1), so the bound grows with depth: layers 3 and 2
-cosine >= 0.999 and relative L2 <= 3e-2, layer 1 cosine >= 0.998 and relative L2 <= 8e-2 (the
+per layer they pass (dO, then dz2, then dz1), so the bound grows with depth: layer 3 cosine >=
+0.999 and relative L2 <= 3e-2, layer 2 cosine >= 0.999 and relative L2 <= 5e-2, layer 1 cosine
+>= 0.998 and relative L2 <= 8e-2 (the
 layer-1 gradients are sums over thousands of cells with heavy cancellation, which magnifies the
 relative effect of the per-element rounding).
 Restriction and the velocity correction are FP32 and held to 1e-6 / 1e-5.
@@ -72,7 +73,7 @@ def test_gradients_match_oracle(seed):
     target = (ut.astype(np.float64) - u) / DS
     ref_loss, ref_grads = K.loss_and_grad(x0, target, mask, params)
     assert abs(loss - ref_loss) < 2e-2 * ref_loss
-    bounds = {1: (0.998, 8e-2), 2: (0.999, 3e-2), 3: (0.999, 3e-2)}
+    bounds = {1: (0.998, 8e-2), 2: (0.999, 5e-2), 3: (0.999, 3e-2)}
     for name, g, r in zip(["W1", "b1", "W2", "b2", "W3", "b3"], grads, ref_grads):
         g, r = g.reshape(-1), r.reshape(-1)
         cos_min, rel_max = bounds[int(name[1])]
