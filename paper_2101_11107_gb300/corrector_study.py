@@ -131,17 +131,24 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         bf = lbm.Batch([fine], graph_steps=2 * apply_every)
         bc = lbm.Batch([coarse], graph_steps=apply_every)
         fmask = tensors_mask(gf)
+        max_du = 0.0
         for t in range(apply_every, n_c + 1, apply_every):
             bf.step(2 * apply_every)
             bc.step(apply_every)
             fr, fu = fine.macroscopic_tensors()
             _, cu = lbm.restrict(fr, fu, fmask)
             rho, u = coarse.macroscopic_tensors()
+            if not (torch.isfinite(u).all() and torch.isfinite(cu).all()):
+                log(f"seed {s}: non-finite state at coarse step {t}; its remaining samples are dropped")
+                break
+            du = (cu - u) * masks[s]
+            max_du = max(max_du, float(du.abs().max()))
             if t > n_c - 2 * period_c:
                 idx = cells[s]
                 data.append((s, rho.reshape(-1)[idx].clone(), u.reshape(3, -1)[:, idx].clone(),
                              cu.reshape(3, -1)[:, idx].clone()))
-            coarse.apply_velocity_correction((cu - u) * masks[s])  # pull onto the fine state
+            coarse.apply_velocity_correction(du)  # pull onto the fine state
+        log(f"seed {s}: max |ideal du| {max_du:.4f}, fluid fine {gf.nfluid} coarse {gc.nfluid}")
         bf.close()
         bc.close()
     torch.cuda.synchronize()
@@ -172,6 +179,8 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         m, rho, u, ut = dense(data[rng.integers(len(data))])
         step_lr = lr if k < 0.7 * train_steps else lr * 0.2
         losses.append(net.train_step(rho, u, ut, step_lr, mask=m))
+        if not np.isfinite(losses[-1]):
+            raise RuntimeError(f"training diverged at step {k}")
     torch.cuda.synchronize()
     train_s = time.time() - t2
     log(f"training: {train_steps} steps in {train_s:.1f} s, loss {np.mean(losses[:50]):.4f} -> "
