@@ -252,14 +252,16 @@ void lbm_batch_destroy(lbm_batch* batch);
  *     multiples of 4): the network is evaluated on the tiles near its fluid (for training over
  *     several geometries give the union of their masks); the scales; initial params (copied).
  *     Memory through the allocator callbacks.
- *   The calls below take a dense device cell mask (nonzero = fluid, inside the creation mask),
- *   or NULL for the creation mask.
+ *   The calls below take a dense device cell mask (nonzero = fluid, inside the creation mask;
+ *   NULL: the creation mask) for the input features, and an output mask (nonzero = cells the
+ *   correction and the loss act on, within the cell mask; NULL: the cell mask).
  *   lbm_corrector_forward: rho[n], u[3][n] dense device fields -> du[3][n] device.
  *   lbm_corrector_gradients: loss L = mean over fluid cells and components of
  *     (O[0:3] - (u_target - u)/du_scale)^2 and dL/dparams (host, FP32); waits.
  *   lbm_corrector_train_step: the same, then one Adam step (b1 0.9, b2 0.999, eps 1e-8) with
  *     learning rate lr; *loss (may be NULL) gets L before the update.
- *   lbm_corrector_apply: rho, u of the domain's current level -> du -> lbm_apply_velocity_correction.
+ *   lbm_corrector_apply: rho, u of the domain's current level -> du (on out_mask, device, may be
+ *     NULL) -> lbm_apply_velocity_correction.
  *   lbm_apply_velocity_correction: the post-collision populations of the previous level gain
  *     f_eq(rho, u + du) - f_eq(rho, u) at every fluid cell except inlet and outlet cells (whose
  *     unknowns the closures rebuild each step; rho, u of the current level); du are
@@ -275,13 +277,13 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
                                 lbm_free_fn release, void* alloc_ctx, void* cuda_stream, lbm_corrector** out);
 lbm_status lbm_corrector_get_params(lbm_corrector* c, float* params);
 lbm_status lbm_corrector_set_params(lbm_corrector* c, const float* params);
-lbm_status lbm_corrector_forward(lbm_corrector* c, const uint8_t* mask, const float* rho, const float* u,
-                                 float* du);
-lbm_status lbm_corrector_gradients(lbm_corrector* c, const uint8_t* mask, const float* rho, const float* u,
-                                   const float* u_target, float* grad, double* loss);
-lbm_status lbm_corrector_train_step(lbm_corrector* c, const uint8_t* mask, const float* rho, const float* u,
-                                    const float* u_target, double lr, double* loss);
-lbm_status lbm_corrector_apply(lbm_corrector* c, lbm_domain* dom);
+lbm_status lbm_corrector_forward(lbm_corrector* c, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
+                                 const float* u, float* du);
+lbm_status lbm_corrector_gradients(lbm_corrector* c, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
+                                   const float* u, const float* u_target, float* grad, double* loss);
+lbm_status lbm_corrector_train_step(lbm_corrector* c, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
+                                    const float* u, const float* u_target, double lr, double* loss);
+lbm_status lbm_corrector_apply(lbm_corrector* c, lbm_domain* dom, const uint8_t* out_mask);
 void lbm_corrector_destroy(lbm_corrector* c);
 lbm_status lbm_apply_velocity_correction(lbm_domain* dom, const float* du, int32_t device_ptrs);
 lbm_status lbm_restrict(const float* fine_rho, const float* fine_u, const uint8_t* fine_mask, int32_t fnx,

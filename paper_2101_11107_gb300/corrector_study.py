@@ -80,6 +80,20 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     def tensors_mask(g):
         return torch.from_numpy(np.ascontiguousarray(g.mask > 0).astype(np.uint8)).cuda()
 
+    def bulk_mask(g):
+        """Fluid cells whose 26 neighbours are all fluid (cells outside the box count as solid):
+        the cells the correction acts on."""
+        fl = np.pad(g.mask > 0, 1)
+        b = fl[1:-1, 1:-1, 1:-1].copy()
+        nz, ny, nx = g.mask.shape
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    b &= fl[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+        return torch.from_numpy(b.astype(np.uint8)).cuda()
+
+    clip = 2.0 * DU_SCALE
+
     def simulate(gf, gc, corrector=None, times=None):
         """Fine, coarse (and optionally corrected coarse) runs over n_c coarse steps; returns the
         samples at `times` as dicts of CUDA tensors.  A corrected run that turns non-finite falls
@@ -91,6 +105,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         bf = lbm.Batch([fine], graph_steps=2 * apply_every)
         bc = lbm.Batch([coarse], graph_steps=apply_every)
         fmask = tensors_mask(gf)
+        bmask = bulk_mask(gc)
         out = []
         state = {"fallback": None}
         for t in range(apply_every, n_c + 1, apply_every):
@@ -98,7 +113,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             bc.step(apply_every)
             if corrector is not None and state["fallback"] is None and t >= apply_from:
                 rho0, u0 = coarse.macroscopic_tensors()
-                corrector.apply(coarse)
+                corrector.apply(coarse, out_mask=bmask)
                 if coarse.diagnostics(raise_unstable=False)["n_nonfinite"]:
                     coarse.init_equilibrium(rho0, u0)
                     state["fallback"] = t
@@ -120,11 +135,12 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     union = np.zeros(pairs[train_seeds[0]][1].mask.shape, bool)
     for s in pairs:
         union |= pairs[s][1].mask > 0
-    masks, cells, data = {}, {}, []
+    masks, bulks, cells, data = {}, {}, {}, []
     t1 = time.time()
     for s in train_seeds:
         gf, gc = pairs[s]
         masks[s] = tensors_mask(gc)
+        bulks[s] = bulk_mask(gc)
         cells[s] = torch.nonzero(masks[s].reshape(-1)).reshape(-1)
         fine = lbm.Domain.from_geometry(gf)
         coarse = lbm.Domain.from_geometry(gc)
@@ -141,7 +157,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             if not (torch.isfinite(u).all() and torch.isfinite(cu).all()):
                 log(f"seed {s}: non-finite state at coarse step {t}; its remaining samples are dropped")
                 break
-            du = (cu - u) * masks[s]
+            du = torch.clamp(cu - u, -clip, clip) * bulks[s]
             max_du = max(max_du, float(du.abs().max()))
             if t > n_c - 2 * period_c:
                 idx = cells[s]
@@ -167,7 +183,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         d_rho.view(-1)[idx] = r
         d_u.view(3, -1)[:, idx] = uu
         d_ut.view(3, -1)[:, idx] = ut
-        return masks[s], d_rho, d_u, d_ut
+        return masks[s], bulks[s], d_rho, d_u, d_ut
 
     # ---------------------------------------------------------------- training
     net = lbm.Corrector(union.astype(np.uint8), I.corrector_init_params(0), U_SCALE, RHO_SCALE, DU_SCALE)
@@ -176,9 +192,9 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     torch.cuda.synchronize()
     t2 = time.time()
     for k in range(train_steps):
-        m, rho, u, ut = dense(data[rng.integers(len(data))])
+        m, bm, rho, u, ut = dense(data[rng.integers(len(data))])
         step_lr = lr if k < 0.7 * train_steps else lr * 0.2
-        losses.append(net.train_step(rho, u, ut, step_lr, mask=m))
+        losses.append(net.train_step(rho, u, ut, step_lr, mask=m, out_mask=bm))
         if not np.isfinite(losses[-1]):
             raise RuntimeError(f"training diverged at step {k}")
     torch.cuda.synchronize()
@@ -191,6 +207,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     for s in test_seeds:
         gf, gc = pairs[s]
         cm = gc.mask
+        bm_eval = bulk_mask(gc)
         plain = simulate(gf, gc)
         corr = simulate(gf, gc, corrector=net)
         e_plain, e_corr, si_plain, si_corr = [], [], [], []
@@ -218,7 +235,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             for t in range(chunk, steps + 1, chunk):
                 b.step(chunk)
                 if name == "coarse+corrector" and t >= apply_from:
-                    net.apply(dom)
+                    net.apply(dom, out_mask=bm_eval)
             ev1.record()
             torch.cuda.synchronize()
             times[name] = ev0.elapsed_time(ev1) / 1e3

@@ -424,9 +424,8 @@ struct lbm_corrector {
         return e;
     }
     // loss and gradients into `grad` (FP32, parameter layout), loss into `loss`
-    cudaError_t backward(const uint8_t* cmask, const float* uu, const float* ut)
+    cudaError_t backward(const uint8_t* mk, const float* uu, const float* ut)
     {
-        const uint8_t* mk = cmask ? cmask : mask;
         cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * NP, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
@@ -582,25 +581,26 @@ lbm_status lbm_corrector_set_params(lbm_corrector* K, const float* params)
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const float* rho, const float* u, float* du)
+lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
+                                 const float* u, float* du)
 {
     if (!K || !rho || !u || !du) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = K->forward(mask, rho, u);
+    const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
     if (e == cudaSuccess) {
-        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, mask ? mask : K->mask, K->n_cells, K->du_scale,
-                                                                 K->clip, du);
+        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, om, K->n_cells, K->du_scale, K->clip, du);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector forward: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const float* rho, const float* u,
-                                   const float* u_target, float* grad, double* loss)
+lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
+                                   const float* u, const float* u_target, float* grad, double* loss)
 {
     if (!K || !rho || !u || !u_target || !grad || !loss) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = K->forward(mask, rho, u);
-    if (e == cudaSuccess) e = K->backward(mask, u, u_target);
+    if (e == cudaSuccess) e = K->backward(out_mask ? out_mask : (mask ? mask : K->mask), u, u_target);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, K->grad, sizeof(float) * NP, cudaMemcpyDeviceToHost, K->stream);
     double l = 0.0;
     unsigned long long cnt = 0;
@@ -612,13 +612,13 @@ lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const 
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const float* rho, const float* u,
-                                    const float* u_target, double lr, double* loss)
+lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
+                                    const float* u, const float* u_target, double lr, double* loss)
 {
     if (!K || !rho || !u || !u_target) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     if (!(lr > 0.0)) return nn_fail(LBM_ERR_INVALID_ARG, "lr must be > 0");
     cudaError_t e = K->forward(mask, rho, u);
-    if (e == cudaSuccess) e = K->backward(mask, u, u_target);
+    if (e == cudaSuccess) e = K->backward(out_mask ? out_mask : (mask ? mask : K->mask), u, u_target);
     K->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float bc1 = 1.0f - std::pow(b1, (float)K->adam_t), bc2 = 1.0f - std::pow(b2, (float)K->adam_t);
@@ -638,7 +638,7 @@ lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom)
+lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t* out_mask)
 {
     if (!K || !dom) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     lbm_info I{};
@@ -647,7 +647,7 @@ lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom)
         return nn_fail(LBM_ERR_INVALID_ARG, "the domain's box differs from the corrector's");
     lbm_status s = lbm_get_macroscopic(dom, K->rho, K->u, 1, 1);
     if (s) return s;
-    s = lbm_corrector_forward(K, nullptr, K->rho, K->u, K->du);
+    s = lbm_corrector_forward(K, nullptr, out_mask, K->rho, K->u, K->du);
     if (s) return s;
     return lbm_apply_velocity_correction(dom, K->du, 1);
 }

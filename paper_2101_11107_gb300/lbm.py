@@ -111,10 +111,10 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.POINTER(vp)]
     L.lbm_corrector_get_params.argtypes = [vp, vp]
     L.lbm_corrector_set_params.argtypes = [vp, vp]
-    L.lbm_corrector_forward.argtypes = [vp, vp, vp, vp, vp]
-    L.lbm_corrector_gradients.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
-    L.lbm_corrector_train_step.argtypes = [vp, vp, vp, vp, vp, dbl, ctypes.POINTER(dbl)]
-    L.lbm_corrector_apply.argtypes = [vp, vp]
+    L.lbm_corrector_forward.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.lbm_corrector_gradients.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    L.lbm_corrector_train_step.argtypes = [vp, vp, vp, vp, vp, vp, dbl, ctypes.POINTER(dbl)]
+    L.lbm_corrector_apply.argtypes = [vp, vp, vp]
     L.lbm_corrector_destroy.argtypes = [vp]
     L.lbm_corrector_destroy.restype = None
     L.lbm_apply_velocity_correction.argtypes = [vp, vp, i32]
@@ -380,31 +380,32 @@ class Corrector:
     def _p(t):
         return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
-    def forward(self, rho, u, mask=None):
-        """du (3,nz,ny,nx) CUDA tensor; mask: optional dense uint8 CUDA tensor of the cells."""
+    def forward(self, rho, u, mask=None, out_mask=None):
+        """du (3,nz,ny,nx) CUDA tensor; mask / out_mask: optional dense uint8 CUDA tensors of the
+        feature cells and of the cells the correction acts on."""
         import torch
         du = torch.empty_like(u, dtype=torch.float32)
-        _check(load_library().lbm_corrector_forward(self._h, self._p(mask), self._p(rho.contiguous()),
+        _check(load_library().lbm_corrector_forward(self._h, self._p(mask), self._p(out_mask), self._p(rho.contiguous()),
                                                     self._p(u.contiguous()), self._p(du)))
         return du
 
-    def gradients(self, rho, u, u_target, mask=None):
+    def gradients(self, rho, u, u_target, mask=None, out_mask=None):
         g = np.zeros(self.n_params, np.float32)
         loss = ctypes.c_double()
-        _check(load_library().lbm_corrector_gradients(self._h, self._p(mask), self._p(rho.contiguous()),
-                                                      self._p(u.contiguous()), self._p(u_target.contiguous()),
-                                                      _ptr(g), ctypes.byref(loss)))
+        _check(load_library().lbm_corrector_gradients(self._h, self._p(mask), self._p(out_mask),
+                                                      self._p(rho.contiguous()), self._p(u.contiguous()),
+                                                      self._p(u_target.contiguous()), _ptr(g), ctypes.byref(loss)))
         return loss.value, unflatten_params(g)
 
-    def train_step(self, rho, u, u_target, lr, mask=None):
+    def train_step(self, rho, u, u_target, lr, mask=None, out_mask=None):
         loss = ctypes.c_double()
-        _check(load_library().lbm_corrector_train_step(self._h, self._p(mask), self._p(rho.contiguous()),
-                                                       self._p(u.contiguous()), self._p(u_target.contiguous()),
-                                                       float(lr), ctypes.byref(loss)))
+        _check(load_library().lbm_corrector_train_step(self._h, self._p(mask), self._p(out_mask),
+                                                       self._p(rho.contiguous()), self._p(u.contiguous()),
+                                                       self._p(u_target.contiguous()), float(lr), ctypes.byref(loss)))
         return loss.value
 
-    def apply(self, domain):
-        _check(load_library().lbm_corrector_apply(self._h, domain._h))
+    def apply(self, domain, out_mask=None):
+        _check(load_library().lbm_corrector_apply(self._h, domain._h, self._p(out_mask)))
 
     def params(self):
         vec = np.zeros(self.n_params, np.float32)
