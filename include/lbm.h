@@ -125,6 +125,9 @@ void lbm_default_params(lbm_params* p);
  *   inlet_center[3], inlet_radius: the inflow profile u = U(n) 2 (1 - r^2/R^2) n_in, r the
  *     distance from the cell centre to inlet_center in the inlet plane (0 beyond R).  May be
  *     NULL / ignored when the mask has no inlet cells.
+ *   tau_cell[nx*ny*nz]: optional relaxation time per cell (a viscosity field, e.g. an absorbing
+ *     layer before an outlet; > 1/2 at fluid cells); the second-order rate of a cell is then
+ *     1/tau_cell.  NULL: params->tau everywhere.
  *   params: see lbm_params; NULL means lbm_default_params.
  *   alloc/release/alloc_ctx: device allocator (both NULL: cudaMalloc / cudaFree).
  *   cuda_stream: cudaStream_t for all work of the domain (NULL: legacy default stream).
@@ -134,9 +137,9 @@ void lbm_default_params(lbm_params* p);
 lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz,
                              const int64_t* link_cell, const uint8_t* link_dir,
                              const double* link_q, int64_t n_links, const double* inlet_center,
-                             double inlet_radius, const lbm_params* params, lbm_alloc_fn alloc,
-                             lbm_free_fn release, void* alloc_ctx, void* cuda_stream,
-                             lbm_domain** out);
+                             double inlet_radius, const double* tau_cell, const lbm_params* params,
+                             lbm_alloc_fn alloc, lbm_free_fn release, void* alloc_ctx,
+                             void* cuda_stream, lbm_domain** out);
 
 /*
  * Sets the inflow waveform (Sec. 2.2: inflow curve over one cycle):

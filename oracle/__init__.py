@@ -27,7 +27,7 @@ def lib():
         L.oracle_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ip,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                     dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, ctypes.c_double,
-                                    ctypes.c_double, ctypes.c_char_p, ctypes.c_int]
+                                    ctypes.c_double, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
         L.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         L.oracle_macroscopic.argtypes = [ctypes.c_void_p, dp, dp]
@@ -173,7 +173,7 @@ class Case:
 
     def __init__(self, mask, periodic=(0, 0, 0), links=None, inlet_center=(0.0, 0.0, 0.0),
                  inlet_radius=1.0, tau=0.6, omega_hi=(1.0, 1.0, 1.0, 1.0), g0=(0.0, 0.0, 0.0),
-                 gamp=(0.0, 0.0, 0.0), gomega=0.0, rho_out=1.0):
+                 gamp=(0.0, 0.0, 0.0), gomega=0.0, rho_out=1.0, tau_cell=None):
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         assert mask.ndim == 3
         self.shape = mask.shape
@@ -194,9 +194,12 @@ class Case:
         g0a, g0p = _d(g0)
         ga, gap = _d(gamp)
         err = ctypes.create_string_buffer(256)
+        tc = None if tau_cell is None else np.ascontiguousarray(tau_cell, dtype=np.float64).reshape(-1)
+        self._tc = tc
         h = lib().oracle_create(nx, ny, nz, mask.ctypes.data, perp, lc.ctypes.data, ld.ctypes.data,
                                 lq.ctypes.data, len(lc), icp, float(inlet_radius), float(tau), ohp,
-                                g0p, gap, float(gomega), float(rho_out), err, 256)
+                                g0p, gap, float(gomega), float(rho_out),
+                                None if tc is None else tc.ctypes.data, err, 256)
         if not h:
             raise ValueError("oracle_create: " + err.value.decode())
         self._h = h

@@ -370,6 +370,8 @@ typedef struct {
     double* qlink;    /* [nfluid][27], q of the wall link whose unknown is direction i; 0 = none */
     double *f, *fpost;
     double s[NQ];
+    double* tau_cell; /* [nfluid] relaxation time of each cell (NULL: tau everywhere) */
+    double omega_hi[4];
     double g0[3], gamp[3], gomega, rho_out;
     double wa[16], wb[16], wP, wpeak;
     int wnh, has_wave;
@@ -437,6 +439,7 @@ void oracle_destroy(oracle_case* C)
     free(C->qlink);
     free(C->f);
     free(C->fpost);
+    free(C->tau_cell);
     free(C);
 }
 
@@ -444,7 +447,7 @@ oracle_case* oracle_create(int nx, int ny, int nz, const uint8_t* mask, const in
                            const int64_t* link_cell, const uint8_t* link_dir, const double* link_q,
                            int64_t n_links, const double* inlet_center, double inlet_radius,
                            double tau, const double* omega_hi, const double* g0, const double* gamp,
-                           double gomega, double rho_out, char* err, int errlen)
+                           double gomega, double rho_out, const double* tau_box, char* err, int errlen)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0 || tau <= 0.5) {
         set_err(err, errlen, "bad box size or tau <= 1/2");
@@ -538,6 +541,21 @@ oracle_case* oracle_create(int nx, int ny, int nz, const uint8_t* mask, const in
         C->qlink[k * NQ + alpha] = q;
     }
     oracle_rates(tau, omega_hi, C->s);
+    for (int k = 0; k < 4; ++k) C->omega_hi[k] = omega_hi[k];
+    /* an optional relaxation time per cell (a viscosity field, e.g. an absorbing layer before an
+     * outlet); the second-order rate of the cell is then 1/tau_cell */
+    if (tau_box) {
+        C->tau_cell = (double*)malloc(sizeof(double) * (size_t)(nf ? nf : 1));
+        for (int64_t k = 0; k < nf; ++k) {
+            double t = tau_box[C->cell[k]];
+            if (!(t > 0.5)) {
+                set_err(err, errlen, "tau_cell must be > 1/2 at fluid cells");
+                oracle_destroy(C);
+                return NULL;
+            }
+            C->tau_cell[k] = t;
+        }
+    }
     for (int d = 0; d < 3; ++d) {
         C->g0[d] = g0[d];
         C->gamp[d] = gamp[d];
@@ -607,7 +625,15 @@ void oracle_step(oracle_case* C, int64_t nsteps)
         double g[3];
         gforce(C, C->n, g);
 #pragma omp parallel for schedule(static)
-        for (int64_t k = 0; k < nf; ++k) oracle_collide(C->f + k * NQ, g, C->s, C->fpost + k * NQ);
+        for (int64_t k = 0; k < nf; ++k) {
+            if (C->tau_cell) {
+                double sk[NQ];
+                oracle_rates(C->tau_cell[k], C->omega_hi, sk);
+                oracle_collide(C->f + k * NQ, g, sk, C->fpost + k * NQ);
+            } else {
+                oracle_collide(C->f + k * NQ, g, C->s, C->fpost + k * NQ);
+            }
+        }
         stream(C);
         C->n += 1;
         apply_open_boundaries(C, C->n);

@@ -504,6 +504,8 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
     const uint32_t wm = word & WORD_WALL_MASK;
     const uint32_t n = (uint32_t)v.n_slots;
     float d[Q];
+    LevelArgs la = a;
+    if (word & WORD_OWN_TAU) la.s2 = __ldg(v.s2_cell + slot);
     if (SCHEME == LBM_SCHEME_ESOTERIC) {
         const int32_t row = __ldg(v.nb8 + brick * 8u + (lane & 7u));
         uint32_t cs[8];
@@ -511,8 +513,8 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         if (!fluid) return;
         fetch_et<ST, true>(dst, n, cs, wm, a.parity, d);
         const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
-        if (FAST) collide_fast(d, a);
-        else collide(d, a);
+        if (FAST) collide_fast(d, la);
+        else collide(d, la);
         store_et<ST>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t rec = (uint32_t)v.aux[slot];
@@ -526,8 +528,8 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
         if (!fluid) return;
         if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
-        if (FAST) collide_fast(d, a);
-        else collide(d, a);
+        if (FAST) collide_fast(d, la);
+        else collide(d, la);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
     }

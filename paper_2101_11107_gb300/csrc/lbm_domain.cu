@@ -186,9 +186,9 @@ const char* lbm_last_error(void) { return g_last_error.c_str(); }
 
 lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz, const int64_t* link_cell,
                              const uint8_t* link_dir, const double* link_q, int64_t n_links,
-                             const double* inlet_center, double inlet_radius, const lbm_params* params,
-                             lbm_alloc_fn alloc, lbm_free_fn release, void* alloc_ctx, void* cuda_stream,
-                             lbm_domain** out)
+                             const double* inlet_center, double inlet_radius, const double* tau_cell,
+                             const lbm_params* params, lbm_alloc_fn alloc, lbm_free_fn release, void* alloc_ctx,
+                             void* cuda_stream, lbm_domain** out)
 {
     g_last_error.clear();
     if (!out) return fail(LBM_ERR_INVALID_ARG, "out is NULL");
@@ -307,12 +307,19 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     fl_slot.reserve((size_t)n_fluid);
     fl_box.reserve((size_t)n_fluid);
     int64_t n_wall = 0;
+    std::vector<float> s2_cell(tau_cell ? (size_t)n_active_slots : 1, 0.0f);
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 const int64_t bi = x + (int64_t)nx * (y + (int64_t)ny * z);
                 if (!mask[bi]) continue;
                 uint32_t w = WORD_FLUID;
+                if (tau_cell && tau_cell[bi] != P.tau) {
+                    if (!(tau_cell[bi] > 0.5) || !std::isfinite(tau_cell[bi]))
+                        return fail(LBM_ERR_INVALID_ARG, "tau_cell must be > 1/2 at fluid cells");
+                    w |= WORD_OWN_TAU;
+                    s2_cell[(size_t)slot_of(x, y, z)] = (float)(1.0 / tau_cell[bi]);
+                }
                 for (int i = 0; i < Q; ++i)
                     if (i != 13 && shifted_fluid(x, y, z, i, -1) < 0) w |= 1u << i;
                 if (w & WORD_WALL_MASK) ++n_wall;
@@ -425,6 +432,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     int32_t* d_nbr = nullptr;
     int32_t* d_nb8 = nullptr;
     uint32_t* d_word = nullptr;
+    float* d_s2 = nullptr;
     int32_t* d_aux = nullptr;
     float* d_bq = nullptr;
     float* d_io_phi = nullptr;
@@ -433,6 +441,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     if (!st) st = upload(D, &d_nbr, nbr, "brick neighbours");
     if (!st) st = upload(D, &d_nb8, nb8, "brick corner neighbours");
     if (!st) st = upload(D, &d_word, word, "cell words");
+    if (!st) st = upload(D, &d_s2, s2_cell, "cell relaxation rates");
     if (!st) st = upload(D, &d_aux, aux, "aux index");
     if (!st) st = upload(D, &d_bq, bq, "Bouzidi q");
     if (!st) st = upload(D, &d_io_phi, io_phi, "inlet profile");
@@ -478,6 +487,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     v.nb8 = d_nb8;
     v.side = D->d_side;
     v.word = d_word;
+    v.s2_cell = d_s2;
     v.aux = d_aux;
     v.bq = d_bq;
     v.n_bq = std::max<int64_t>(n_bq, 1);

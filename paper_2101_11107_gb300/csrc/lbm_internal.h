@@ -34,8 +34,10 @@ constexpr int BRICK_CELLS = 64;
 // Per-slot cell word (active bricks).
 //   bits 0..26  wall mask: bit i set <=> the pull source x - c_i is not a fluid cell
 //   bits 27..28 kind (plain / Bouzidi / inlet / outlet)
+//   bit 29      the cell relaxes with its own second-order rate s2_cell[slot]
 //   bit 31      the slot is a fluid cell (updated every step); solid slots have word 0
 constexpr uint32_t WORD_FLUID = 1u << 31;
+constexpr uint32_t WORD_OWN_TAU = 1u << 29;  // the cell has its own relaxation time (s2_cell)
 constexpr uint32_t WORD_WALL_MASK = (1u << 27) - 1u;
 constexpr int WORD_KIND_SHIFT = 27;
 enum CellKind { KIND_PLAIN = 0, KIND_BOUZIDI = 1, KIND_INLET = 2, KIND_OUTLET = 3 };
@@ -48,6 +50,7 @@ struct DomainView {
     const int32_t* nb8;     // twist: [n_bricks][8] brick at offset (ex,ey,ez) in {0,1}^3, never -1
     const uint32_t* word;   // [64 n_bricks]
     const int32_t* aux;     // [64 n_bricks] record of a Bouzidi or open-boundary cell
+    const float* s2_cell;   // [64 n_bricks] second-order rate of cells with WORD_OWN_TAU
     const float* bq;        // [27][n_bq] Bouzidi q of the link whose unknown is i (0: halfway BB)
     void* side;             // twist: [27][n_bq] f*_i of the previous step at Bouzidi cells (storage type)
     int64_t n_bq;

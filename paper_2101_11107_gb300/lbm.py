@@ -83,7 +83,7 @@ def load_library(path: str = LIB_PATH):
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     L.lbm_default_params.argtypes = [ctypes.POINTER(Params)]
     L.lbm_default_params.restype = None
-    L.lbm_create_domain.argtypes = [vp, i32, i32, i32, vp, vp, vp, i64, vp, dbl, ctypes.POINTER(Params),
+    L.lbm_create_domain.argtypes = [vp, i32, i32, i32, vp, vp, vp, i64, vp, dbl, vp, ctypes.POINTER(Params),
                                     ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(vp)]
     L.lbm_set_inlet_waveform.argtypes = [vp, vp, vp, i32, dbl, dbl]
     L.lbm_init_equilibrium.argtypes = [vp, vp, vp, i32]
@@ -169,7 +169,8 @@ class Domain:
 
     def __init__(self, mask, periodic=(0, 0, 0), links=None, inlet_center=None, inlet_radius=0.0,
                  tau=0.6, omega_hi=(1.0, 1.0, 1.0, 1.0), force=(0.0, 0.0, 0.0), force_amp=(0.0, 0.0, 0.0),
-                 force_omega=0.0, rho_out=1.0, storage="fp32", scheme="esoteric", device=None, stream=None):
+                 force_omega=0.0, rho_out=1.0, storage="fp32", scheme="esoteric", tau_cell=None, device=None,
+                 stream=None):
         import torch
         L = load_library()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -202,11 +203,12 @@ class Domain:
             lq = np.ascontiguousarray(links[2], dtype=np.float64)
             n_links = len(lc)
         ic = None if inlet_center is None else np.ascontiguousarray(inlet_center, dtype=np.float64)
+        tc = None if tau_cell is None else np.ascontiguousarray(tau_cell, dtype=np.float64)
         self._alloc = TorchAllocator(self.device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(L.lbm_create_domain(_ptr(mask), nx, ny, nz, _ptr(lc), _ptr(ld), _ptr(lq), n_links, _ptr(ic),
-                                       float(inlet_radius), ctypes.byref(p), self._alloc.alloc_fn,
+                                       float(inlet_radius), _ptr(tc), ctypes.byref(p), self._alloc.alloc_fn,
                                        self._alloc.free_fn, None, ctypes.c_void_p(self.stream.cuda_stream),
                                        ctypes.byref(h)))
         self._h = h
@@ -215,7 +217,7 @@ class Domain:
     def from_geometry(cls, g, storage="fp32", scheme="esoteric", **kw):
         dom = cls(g.mask, periodic=g.periodic, links=g.links, inlet_center=g.inlet_center,
                   inlet_radius=g.inlet_radius, tau=g.tau, force=g.g0, force_amp=g.gamp,
-                  force_omega=g.gomega, storage=storage, scheme=scheme, **kw)
+                  force_omega=g.gomega, storage=storage, scheme=scheme, tau_cell=g.tau_cell, **kw)
         if g.wave is not None:
             a, b, P, up = g.wave
             dom.set_inlet_waveform(a, b, P, up)

@@ -62,7 +62,7 @@ def _create(L, mask, links=None, params=None, inlet_center=None, inlet_radius=0.
     ic = None if inlet_center is None else np.ascontiguousarray(inlet_center, np.float64)
     h = ctypes.c_void_p()
     st = L.lbm_create_domain(lbm._ptr(mask), nx, ny, nz, lbm._ptr(lc), lbm._ptr(ld), lbm._ptr(lq), n,
-                             lbm._ptr(ic), inlet_radius, ctypes.byref(p), lbm.ALLOC_FN(0), lbm.FREE_FN(0),
+                             lbm._ptr(ic), inlet_radius, None, ctypes.byref(p), lbm.ALLOC_FN(0), lbm.FREE_FN(0),
                              None, None, ctypes.byref(h))
     return st, L.lbm_last_error().decode(), h
 

@@ -114,7 +114,7 @@ def test_velocity_correction_matches_oracle(scheme):
     g = I.aneurysm(8, edge=64, period=200.0, reynolds=30.0)
     dom = lbm.Domain.from_geometry(g, scheme=scheme)
     ref = oracle.Case(g.mask, periodic=g.periodic, links=g.links, inlet_center=g.inlet_center,
-                      inlet_radius=g.inlet_radius, tau=g.tau)
+                      inlet_radius=g.inlet_radius, tau=g.tau, tau_cell=g.tau_cell)
     ref.set_waveform(*g.wave)
     dom.step(57)
     ref.step(57)

@@ -35,7 +35,8 @@ def run_pair(g, steps, storage="fp32", init=None, ref_mask=None, scheme="esoteri
     rm = g.mask if ref_mask is None else ref_mask
     links = g.links if ref_mask is None else None
     ref = oracle.Case(rm, periodic=g.periodic, links=links, inlet_center=g.inlet_center,
-                      inlet_radius=g.inlet_radius, tau=g.tau, g0=g.g0, gamp=g.gamp, gomega=g.gomega)
+                      inlet_radius=g.inlet_radius, tau=g.tau, g0=g.g0, gamp=g.gamp, gomega=g.gomega,
+                      tau_cell=g.tau_cell if ref_mask is None else None)
     if g.wave is not None:
         ref.set_waveform(*g.wave)
     if init is not None:

@@ -196,3 +196,30 @@ def test_velocity_correction_sets_velocity():
     r1, u1 = c.macroscopic()
     assert np.allclose(u1[0], 0.01, atol=1e-15) and np.allclose(u1[1], 0.003, atol=1e-15)
     assert abs(r1.sum() - r0.sum()) < 1e-12
+
+
+def test_uniform_tau_field_is_the_same_case():
+    """A relaxation-time field equal to tau everywhere reproduces the uniform case bitwise, and a
+    field with a higher tau in one half damps a shear wave faster there (local viscosity)."""
+    g = I.poiseuille_pipe_32()
+    m = g.mask[:1].copy()
+    a = oracle.Case(m, periodic=g.periodic, tau=g.tau, g0=g.g0)
+    b = oracle.Case(m, periodic=g.periodic, tau=g.tau, g0=g.g0, tau_cell=np.full(m.shape, g.tau))
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.macroscopic()[1], b.macroscopic()[1])
+    c = oracle.Case(m, periodic=g.periodic, tau=g.tau, g0=g.g0, tau_cell=np.where(np.arange(32)[None, None, :] < 16,
+                                                                                    g.tau, 0.9) + 0 * m)
+    c.step(300)
+    a.step(260)
+    ua, uc = a.macroscopic()[1][2, 0], c.macroscopic()[1][2, 0]
+    assert uc[:, 16:].max() < ua[:, 16:].max()
+
+
+def test_outlet_sponge_field():
+    mask = np.zeros((6, 6, 16), np.uint8)
+    mask[1:5, 1:5, :] = 1
+    mask[1:5, 1:5, 0] = 3
+    f = I.outlet_sponge(mask, 0.51, 4.0, 0.61)
+    assert np.allclose(f[:, :, 0], 0.61) and np.allclose(f[:, :, 4:], 0.51)
+    assert np.allclose(f[0, 0, 2], 0.51 + 0.1 * 0.25)
