@@ -321,3 +321,18 @@ def test_batch_rejects_mixed_members():
     for members in ([a, b], [a, c], [a, a]):
         with pytest.raises(lbm.LbmError):
             lbm.Batch(members)
+
+
+def test_aneurysm_re300_runs_stably_with_absorbing_layer():
+    """The coarse synthetic aneurysm at Re 300 (128^3, tau ~ 0.503, the paper's coarse value)
+    runs three cardiac periods (6000 steps) without a non-finite value and without spurious
+    speeds (max |u| stays below three times the peak inflow centreline speed of 0.05)."""
+    g = I.aneurysm(101, edge=128, period=2000, wave_seed=101)
+    dom = lbm.Domain.from_geometry(g)
+    batch = lbm.Batch([dom], graph_steps=100)
+    worst = 0.0
+    for _ in range(60):
+        batch.step(100)
+        d = dom.diagnostics()
+        worst = max(worst, d["max_u"])
+    assert d["n_nonfinite"] == 0 and worst < 0.15, worst
