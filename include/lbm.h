@@ -263,8 +263,9 @@ void lbm_batch_destroy(lbm_batch* batch);
  *     (O[0:3] - (u_target - u)/du_scale)^2 and dL/dparams (host, FP32); waits.
  *   lbm_corrector_train_step: the same, then one Adam step (b1 0.9, b2 0.999, eps 1e-8) with
  *     learning rate lr; *loss (may be NULL) gets L before the update.
- *   lbm_corrector_apply: rho, u of the domain's current level -> du (on out_mask, device, may be
- *     NULL) -> lbm_apply_velocity_correction.
+ *   lbm_corrector_apply: rho, u of the domain's current level -> gain * du (features on mask,
+ *     correction on out_mask; device, may be NULL; gain in (0, 1] nudges instead of replacing)
+ *     -> lbm_apply_velocity_correction.
  *   lbm_apply_velocity_correction: the post-collision populations of the previous level gain
  *     f_eq(rho, u + du) - f_eq(rho, u) at every fluid cell except inlet and outlet cells (whose
  *     unknowns the closures rebuild each step; rho, u of the current level); du are
@@ -286,7 +287,8 @@ lbm_status lbm_corrector_gradients(lbm_corrector* c, const uint8_t* mask, const 
                                    const float* u, const float* u_target, float* grad, double* loss);
 lbm_status lbm_corrector_train_step(lbm_corrector* c, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
                                     const float* u, const float* u_target, double lr, double* loss);
-lbm_status lbm_corrector_apply(lbm_corrector* c, lbm_domain* dom, const uint8_t* out_mask);
+lbm_status lbm_corrector_apply(lbm_corrector* c, lbm_domain* dom, const uint8_t* mask, const uint8_t* out_mask,
+                               double gain);
 void lbm_corrector_destroy(lbm_corrector* c);
 lbm_status lbm_apply_velocity_correction(lbm_domain* dom, const float* du, int32_t device_ptrs);
 lbm_status lbm_restrict(const float* fine_rho, const float* fine_u, const uint8_t* fine_mask, int32_t fnx,

@@ -638,17 +638,25 @@ lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const
     return LBM_OK;
 }
 
-lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t* out_mask)
+lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t* mask, const uint8_t* out_mask,
+                               double gain)
 {
     if (!K || !dom) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    if (!(gain > 0.0 && gain <= 1.0)) return nn_fail(LBM_ERR_INVALID_ARG, "gain must lie in (0, 1]");
     lbm_info I{};
     lbm_get_info(dom, &I);
     if (I.nx != K->box.nx || I.ny != K->box.ny || I.nz != K->box.nz)
         return nn_fail(LBM_ERR_INVALID_ARG, "the domain's box differs from the corrector's");
     lbm_status s = lbm_get_macroscopic(dom, K->rho, K->u, 1, 1);
     if (s) return s;
-    s = lbm_corrector_forward(K, nullptr, out_mask, K->rho, K->u, K->du);
-    if (s) return s;
+    cudaError_t e = K->forward(mask, K->rho, K->u);
+    const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
+    if (e == cudaSuccess) {
+        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, om, K->n_cells, (float)(K->du_scale * gain),
+                                                                 K->clip, K->du);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector apply: ") + cudaGetErrorString(e));
     return lbm_apply_velocity_correction(dom, K->du, 1);
 }
 

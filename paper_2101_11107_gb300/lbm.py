@@ -114,7 +114,7 @@ def load_library(path: str = LIB_PATH):
     L.lbm_corrector_forward.argtypes = [vp, vp, vp, vp, vp, vp]
     L.lbm_corrector_gradients.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
     L.lbm_corrector_train_step.argtypes = [vp, vp, vp, vp, vp, vp, dbl, ctypes.POINTER(dbl)]
-    L.lbm_corrector_apply.argtypes = [vp, vp, vp]
+    L.lbm_corrector_apply.argtypes = [vp, vp, vp, vp, dbl]
     L.lbm_corrector_destroy.argtypes = [vp]
     L.lbm_corrector_destroy.restype = None
     L.lbm_apply_velocity_correction.argtypes = [vp, vp, i32]
@@ -406,8 +406,8 @@ class Corrector:
                                                        self._p(u_target.contiguous()), float(lr), ctypes.byref(loss)))
         return loss.value
 
-    def apply(self, domain, out_mask=None):
-        _check(load_library().lbm_corrector_apply(self._h, domain._h, self._p(out_mask)))
+    def apply(self, domain, mask=None, out_mask=None, gain=1.0):
+        _check(load_library().lbm_corrector_apply(self._h, domain._h, self._p(mask), self._p(out_mask), float(gain)))
 
     def params(self):
         vec = np.zeros(self.n_params, np.float32)

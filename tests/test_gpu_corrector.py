@@ -144,7 +144,7 @@ def test_apply_through_corrector():
     a.step(30)
     b.step(30)
     net = lbm.Corrector(g.mask, params, US, RS, DS)
-    net.apply(a)
+    net.apply(a)  # creation mask, gain 1
     rho, u = b.macroscopic_tensors()
     b.apply_velocity_correction(net.forward(rho, u))
     assert np.array_equal(a.macroscopic()[1], b.macroscopic()[1])
