@@ -5,13 +5,14 @@
 
 Full study: fine 256^3 (tau from Re 300), coarse 128^3 with acoustic scaling (half the steps,
 tau_c - 1/2 = (tau_f - 1/2)/2, the same lattice velocity and waveform over half the period:
-Sec. 2.2.3 and 3.4 of the paper, 0.506 -> 0.503).  Training pairs come from the solver itself,
-in the setting the corrector meets at run time: every 50 coarse steps the coarse run is nudged
-toward the restricted fine state (the velocity-correction step the corrector uses, with gain
-times the ideal correction, at bulk cells), and each pair is the coarse state 50 steps after a
-nudge together with the restricted fine state at that time; pairs from the last two periods of
-32 seeded geometries, stored as fluid-cell lists.  A full replacement every 50 steps (gain 1)
-destabilises the coarse run at tau ~ 0.503.  The corrector (3 conv layers, BF16 tensor cores) is trained on the
+Sec. 2.2.3 and 3.4 of the paper, 0.506 -> 0.503).  Training pairs come from the solver itself:
+plain coarse states and the fine states restricted onto the coarse grid at the same physical
+time, every 50 coarse steps of the last two periods of 32 seeded geometries (stored as
+fluid-cell lists).  The trained network is evaluated two ways: as an output correction of the
+plain coarse run (u_c + du at the sample times), and in the loop, nudging the coarse run every
+50 steps with gain 1/4 after one period of warm-up (a full replacement every 50 steps, or nudges
+in a feedback loop at gain 1/2, destabilise the coarse run at tau ~ 0.503), falling back to the
+plain coarse solver if the state turns non-finite.  The corrector (3 conv layers, BF16 tensor cores) is trained on the
 GPU and applied every 50 coarse steps after one period of warm-up.  Evaluation on 8 held-out
 geometries: relative L2 error of u against the restricted fine run over the coarse fluid cells
 at 10 phases of the last cycle, the similarity index of the paper's Sec. 3.4 (read with the
@@ -59,7 +60,7 @@ def similarity_index(u_hr, u_lr, mask):
 
 
 def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples_per_period, train_steps, lr,
-        apply_every, workers, log, gain=0.5):
+        apply_every, workers, log, gain=0.25):
     import torch
 
     from . import inputs as I
@@ -134,6 +135,8 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         return out
 
     # ---------------------------------------------------------------- training data
+    # plain fine and coarse runs side by side; every interval of the last two periods gives a
+    # pair (coarse state, fine state restricted onto the coarse grid), stored as fluid-cell lists
     union = np.zeros(pairs[train_seeds[0]][1].mask.shape, bool)
     for s in pairs:
         union |= pairs[s][1].mask > 0
@@ -144,31 +147,11 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         masks[s] = tensors_mask(gc)
         bulks[s] = bulk_mask(gc)
         cells[s] = torch.nonzero(masks[s].reshape(-1)).reshape(-1)
-        fine = lbm.Domain.from_geometry(gf)
-        coarse = lbm.Domain.from_geometry(gc)
-        bf = lbm.Batch([fine], graph_steps=2 * apply_every)
-        bc = lbm.Batch([coarse], graph_steps=apply_every)
-        fmask = tensors_mask(gf)
-        max_du = 0.0
-        for t in range(apply_every, n_c + 1, apply_every):
-            bf.step(2 * apply_every)
-            bc.step(apply_every)
-            fr, fu = fine.macroscopic_tensors()
-            _, cu = lbm.restrict(fr, fu, fmask)
-            rho, u = coarse.macroscopic_tensors()
-            if not (torch.isfinite(u).all() and torch.isfinite(cu).all()):
-                log(f"seed {s}: non-finite state at coarse step {t}; its remaining samples are dropped")
-                break
-            du = gain * torch.clamp(cu - u, -clip, clip) * bulks[s]
-            max_du = max(max_du, float(du.abs().max()))
-            if t > n_c - 2 * period_c:
-                idx = cells[s]
-                data.append((s, rho.reshape(-1)[idx].clone(), u.reshape(3, -1)[:, idx].clone(),
-                             cu.reshape(3, -1)[:, idx].clone()))
-            coarse.apply_velocity_correction(du)  # nudge toward the fine state
-        log(f"seed {s}: max |ideal du| {max_du:.4f}, fluid fine {gf.nfluid} coarse {gc.nfluid}")
-        bf.close()
-        bc.close()
+        times = [t for t in range(apply_every, n_c + 1, apply_every) if t > n_c - 2 * period_c]
+        for smp in simulate(gf, gc, times=times):
+            idx = cells[s]
+            data.append((s, smp["rho"].reshape(-1)[idx].clone(), smp["u"].reshape(3, -1)[:, idx].clone(),
+                         smp["u_fine"].reshape(3, -1)[:, idx].clone()))
     torch.cuda.synchronize()
     log(f"training data: {len(data)} samples from {len(train_seeds)} geometries in {time.time() - t1:.1f} s")
     shape = pairs[train_seeds[0]][1].mask.shape
@@ -213,16 +196,18 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         cm_eval = tensors_mask(gc)
         plain = simulate(gf, gc)
         corr = simulate(gf, gc, corrector=net)
-        e_plain, e_corr, si_plain, si_corr = [], [], [], []
+        e_plain, e_corr, e_out, si_plain, si_corr, si_out = [], [], [], [], [], []
+        fl = cm > 0
         for a, b in zip(plain, corr):
             uf = a["u_fine"].cpu().numpy()
             up = a["u"].cpu().numpy()
             uc = b["u"].cpu().numpy()
-            fl = cm > 0
-            e_plain.append(float(np.linalg.norm((up - uf)[:, fl]) / np.linalg.norm(uf[:, fl])))
-            e_corr.append(float(np.linalg.norm((uc - uf)[:, fl]) / np.linalg.norm(uf[:, fl])))
+            uo = (a["u"] + net.forward(a["rho"], a["u"], mask=cm_eval, out_mask=bm_eval)).cpu().numpy()
+            for arr, v in ((e_plain, up), (e_corr, uc), (e_out, uo)):
+                arr.append(float(np.linalg.norm((v - uf)[:, fl]) / np.linalg.norm(uf[:, fl])))
             si_plain.append(similarity_index(uf, up, cm))
             si_corr.append(similarity_index(uf, uc, cm))
+            si_out.append(similarity_index(uf, uo, cm))
         # wall times, no sampling inside
         times = {}
         for name in ("fine", "coarse", "coarse+corrector"):
@@ -258,6 +243,8 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         "apply_every": apply_every, "gain": gain,
         "err_plain_mean": float(np.mean([r["err_plain"] for r in results])),
         "err_corrected_mean": float(np.mean([r["err_corrected"] for r in results])),
+        "err_output_corrected_mean": float(np.mean([r["err_output_corrected"] for r in results])),
+        "si_output_corrected_mean": float(np.mean([r["si_output_corrected"] for r in results])),
         "si_plain_mean": float(np.mean([r["si_plain"] for r in results])),
         "si_corrected_mean": float(np.mean([r["si_corrected"] for r in results])),
         "wall_fine_s": float(np.mean([r["wall_s"]["fine"] for r in results])),
@@ -276,7 +263,7 @@ def main(argv=None):
     ap.add_argument("--workers", type=int, default=16)
     a = ap.parse_args(argv)
     if a.small:
-        cfg = dict(fine_edge=128, period_f=800, reynolds=60.0, train_seeds=list(range(100, 106)),
+        cfg = dict(fine_edge=128, period_f=800, reynolds=60.0, train_seeds=list(range(100, 116)),
                    test_seeds=[200, 201], periods=3, samples_per_period=4, train_steps=1500, lr=2e-3, apply_every=50)
     else:
         cfg = dict(fine_edge=256, period_f=4000, reynolds=300.0, train_seeds=list(range(100, 132)),
