@@ -230,7 +230,9 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             b.close()
         r = {"seed": int(s), "fine_fluid": int(gf.nfluid), "coarse_fluid": int(gc.nfluid), "tau_fine": gf.tau,
              "tau_coarse": gc.tau, "err_plain": float(np.mean(e_plain)), "err_corrected": float(np.mean(e_corr)),
+             "err_output_corrected": float(np.mean(e_out)),
              "si_plain": float(np.mean(si_plain)), "si_corrected": float(np.mean(si_corr)),
+             "si_output_corrected": float(np.mean(si_out)),
              "fallback_at_step": corr[0].get("fallback") if corr else None,
              "wall_s": times}
         log(json.dumps(r))
