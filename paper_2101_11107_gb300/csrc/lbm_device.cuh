@@ -35,6 +35,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -545,6 +547,87 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     step_cell<ST, SCHEME, FAST>(v, src, dst, a, slot, threadIdx.x & 31u);
 }
 
+// Software-pipelined persistent variant of the FP32 esoteric-twist step.  Each CTA walks over
+// chunks of BRICKS bricks; before computing chunk c, every thread issues cp.async copies of the
+// 27 populations its cell of chunk c + gridDim will read (shared memory, one stage per chunk,
+// two stages), so that the next cell's loads are in flight during the current cell's
+// arithmetic without holding registers.  Each thread copies and reads only its own staging
+// slots, so no CTA barrier is needed; and every location of the in-place array is owned by one
+// cell, so prefetching another cell's locations before this cell's stores cannot race.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int BRICKS, int MINB, bool FAST>
+__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
+    k_step_et_pipe(DomainView v, float* __restrict__ pop, LevelArgs a)
+{
+    constexpr int T = BRICKS * BRICK_CELLS;
+    extern __shared__ float stage[];  // [2][27][T]
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const uint32_t n = (uint32_t)v.n_slots;
+    const int64_t n_chunks = (v.n_bricks + BRICKS - 1) / BRICKS;
+    // issue the copies of chunk c into stage st (all lanes run the shuffles)
+    auto prefetch = [&](int64_t c, int st) {
+        const uint32_t slot = (uint32_t)(c * T) + tid;
+        if (slot < (uint32_t)(v.n_bricks * BRICK_CELLS)) {
+            const uint32_t word = __ldg(v.word + slot);
+            const int32_t row = __ldg(v.nb8 + (slot / BRICK_CELLS) * 8u + (lane & 7u));
+            uint32_t cs[8];
+            corner_slots_shfl(row, slot, cs);
+            if (word & WORD_FLUID) {
+                const uint32_t wm = word & WORD_WALL_MASK;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const uint32_t flip = ((uint32_t)a.parity ^ (wm >> i)) & 1u;
+                    const uint32_t dir = flip ? (uint32_t)(Q - 1 - i) : (uint32_t)i;
+                    cp_async4(&stage[(st * Q + i) * T + tid], pop + dir * n + cs[corner_neg(i)]);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    int st = 0;
+    int64_t c = blockIdx.x;
+    if (c < n_chunks) prefetch(c, 0);
+    for (; c < n_chunks; c += gridDim.x) {
+        prefetch(c + gridDim.x, st ^ 1);  // an empty group past the end keeps the count aligned
+        cp_async_wait_one();
+        const uint32_t slot = (uint32_t)(c * T) + tid;
+        if (slot < (uint32_t)(v.n_bricks * BRICK_CELLS)) {
+            const uint32_t word = __ldg(v.word + slot);
+            const int32_t row = __ldg(v.nb8 + (slot / BRICK_CELLS) * 8u + (lane & 7u));
+            uint32_t cs[8];
+            corner_slots_shfl(row, slot, cs);
+            if (word & WORD_FLUID) {
+                const uint32_t wm = word & WORD_WALL_MASK;
+                LevelArgs la = a;
+                if (word & WORD_OWN_TAU) la.s2 = __ldg(v.s2_cell + slot);
+                float d[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) d[i] = stage[(st * Q + i) * T + tid];
+                const uint32_t half = wm ? wall_rules<LBM_STORE_FP32, LBM_SCHEME_ESOTERIC>(v, nullptr, slot, word, a, d) : 0u;
+                if (FAST) collide_fast(d, la);
+                else collide(d, la);
+                store_et<LBM_STORE_FP32>(pop, n, cs, a.parity, d);
+                if (half) {
+                    const uint32_t rec = (uint32_t)v.aux[slot];
+                    const uint32_t nbq = (uint32_t)v.n_bq;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        if (half & (1u << i)) Store<LBM_STORE_FP32>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
+                }
+            }
+        }
+        st ^= 1;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Several domains (esoteric twist, one storage precision) in one launch: the CTAs run over the
 // concatenated brick lists; each warp finds its domain by binary search in the brick prefix
 // sums and updates one of that domain's half-bricks with the domain's own level arguments.
@@ -783,10 +866,37 @@ cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const
     return cudaGetLastError();
 }
 
+template <int BRICKS, int MINB>
+cudaError_t launch_step_et_pipe(const DomainView& v, void* pop, const LevelArgs& a, cudaStream_t s)
+{
+    if (v.n_bricks == 0) return cudaSuccess;
+    constexpr int T = BRICKS * BRICK_CELLS;
+    const size_t smem = sizeof(float) * 2 * Q * T;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_step_et_pipe<BRICKS, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step_et_pipe<BRICKS, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    const int64_t n_chunks = (v.n_bricks + BRICKS - 1) / BRICKS;
+    const int grid = (int)std::min<int64_t>(n_chunks, (int64_t)sms * MINB);
+    if (a.fast_rates)
+        k_step_et_pipe<BRICKS, MINB, true><<<grid, T, smem, s>>>(v, static_cast<float*>(pop), a);
+    else
+        k_step_et_pipe<BRICKS, MINB, false><<<grid, T, smem, s>>>(v, static_cast<float*>(pop), a);
+    return cudaGetLastError();
+}
+
 template <int ST, int SCHEME>
 cudaError_t launch_step_scheme(int config, const DomainView& v, const void* src, void* dst, const LevelArgs& a,
                                cudaStream_t s)
 {
+    if (config == 5) {
+        if (ST == LBM_STORE_FP32 && SCHEME == LBM_SCHEME_ESOTERIC) return launch_step_et_pipe<2, 6>(v, dst, a, s);
+        config = 3;  // the pipelined variant exists for FP32 twist only
+    }
     switch (config) {
     case 0: return launch_step_t<ST, SCHEME, 4, 3>(v, src, dst, a, s);
     case 1: return launch_step_t<ST, SCHEME, 4, 4>(v, src, dst, a, s);

@@ -77,7 +77,7 @@ struct BatchEntry {
     void* pop;  // the domain's in-place population array
 };
 
-constexpr int N_LAUNCH_CONFIGS = 5;
+constexpr int N_LAUNCH_CONFIGS = 6;
 constexpr int DEFAULT_LAUNCH_CONFIG = 3;  // 128 threads, 8 CTAs per SM
 
 // Launchers, one set per storage precision (lbm_step_<storage>.cu).  All enqueue on `stream`

@@ -27,8 +27,8 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_corrector_create", "lbm_corrector_get_params", "lbm_corrector_set_params", "lbm_corrector_forward",
            "lbm_corrector_gradients", "lbm_corrector_train_step", "lbm_corrector_apply", "lbm_corrector_destroy",
            "lbm_apply_velocity_correction", "lbm_restrict"]
-N_LAUNCH_CONFIGS = 5
-LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10"]
+N_LAUNCH_CONFIGS = 6
+LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10", "pipe128x6"]
 SCHEME = {"ab": 0, "esoteric": 1}
 
 
