@@ -38,9 +38,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "womersley_pipe_64x64x256_R28_Wo4_tau0.55"
 METRIC = "fluid MLUPS, D3Q27 CHM-MRT fused stream-collide (% of measured HBM roofline)"
 BYTES_PER_VALUE = {"fp32": 4, "fp16": 2, "bf16": 2}
-# DRAM bytes per launch of the FP32 twist step kernel on this workload, from the ncu capture
-# summarised in profiles/k_step_womersley_fp32_twist.md (80.33 MB read + 25.25 MB write)
-K_STEP_TRAFFIC_BYTES = 105_575_680
+# DRAM bytes per launch of the FP32 twist step kernel in launch config 128x6 on this workload,
+# from the ncu capture summarised in profiles/k_step_womersley_fp32_twist.md
+# (79.99 MB read + 18.77 MB write); reported only when the bench runs that configuration
+K_STEP_TRAFFIC_BYTES = 98_760_192
+K_STEP_TRAFFIC_CONFIG = "128x6"
 
 
 def dist_env():
@@ -385,7 +387,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "bytes_per_update_algorithmic": 216, "wall_s_timed_loop": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": K_STEP_TRAFFIC_BYTES,
+                     "frac": achieved / hbm_peak,
+                     "traffic": K_STEP_TRAFFIC_BYTES if main["launch_config"] == K_STEP_TRAFFIC_CONFIG else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                      "profiles/k_step_womersley_fp32_twist.md)",
                      "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},

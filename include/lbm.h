@@ -206,7 +206,7 @@ lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
  * with a register budget for 3 or 4 resident CTAs per SM; 2, 3, 4 = 128 threads with 6, 8 or
  * 10; 5 = a persistent, software-pipelined variant (128 threads, 6 CTAs per SM; the next cell's
  * populations are copied into shared memory asynchronously while the current one is computed;
- * FP32 esoteric twist only, other domains use 3).  Results do not depend on it.  Default 3.
+ * FP32 esoteric twist only, other domains use 3).  Results do not depend on it.  Default 2.
  * Errors: INVALID_ARG. */
 lbm_status lbm_set_launch_config(lbm_domain* dom, int32_t config);
 

@@ -78,7 +78,7 @@ struct BatchEntry {
 };
 
 constexpr int N_LAUNCH_CONFIGS = 6;
-constexpr int DEFAULT_LAUNCH_CONFIG = 3;  // 128 threads, 8 CTAs per SM
+constexpr int DEFAULT_LAUNCH_CONFIG = 2;  // 128 threads, 6 CTAs per SM
 
 // Launchers, one set per storage precision (lbm_step_<storage>.cu).  All enqueue on `stream`
 // and return the launch status.

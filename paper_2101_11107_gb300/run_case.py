@@ -1,6 +1,6 @@
 """Run a named workload for a few steps on the GPU (for profiling and quick checks).
 
-    python -m paper_2101_11107_gb300.run_case womersley fp32 4 [esoteric|ab]
+    python -m paper_2101_11107_gb300.run_case womersley fp32 4 [esoteric|ab] [launch config name]
     python -m paper_2101_11107_gb300.run_case aneurysm256 fp16 10
 
 Workloads: womersley (64x64x256 pulsatile pipe, radius 28), poiseuille (32x32x64 pipe,
@@ -15,6 +15,7 @@ def main(argv=None):
     storage = argv[1] if len(argv) > 1 else "fp32"
     steps = int(argv[2]) if len(argv) > 2 else 4
     scheme = argv[3] if len(argv) > 3 else "esoteric"
+    config = argv[4] if len(argv) > 4 else None
     from . import build as lib_build
     from . import inputs as I
     from . import lbm
@@ -29,6 +30,8 @@ def main(argv=None):
     else:
         raise SystemExit(f"unknown case {case}")
     dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme)
+    if config is not None:
+        dom.set_launch_config(lbm.LAUNCH_CONFIG_NAMES.index(config))
     dom.step(steps)
     dom.sync()
     info = dom.info()
