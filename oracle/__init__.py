@@ -57,6 +57,13 @@ def lib():
         L.oracle_collide.argtypes = [dp, dp, dp, dp]
         L.oracle_bgk.argtypes = [dp, ctypes.c_double, dp]
         L.oracle_zouhe.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double]
+        L.oracle_feq2.argtypes = [ctypes.c_double, dp, dp]
+        L.oracle_collide_srt2.argtypes = [dp, dp, ctypes.c_double, dp]
+        L.oracle_collide_trt2.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.oracle_trt_minus_rate.restype = ctypes.c_double
+        L.oracle_trt_minus_rate.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.oracle_set_collision.restype = ctypes.c_int
+        L.oracle_set_collision.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -139,6 +146,36 @@ def bgk(f, tau):
     return out
 
 
+def feq2(rho, u):
+    out = np.zeros(27)
+    u, up = _d(u)
+    lib().oracle_feq2(float(rho), up, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def collide_srt2(f, g, tau):
+    f, fp = _d(f)
+    g, gp = _d(g)
+    out = np.zeros(27)
+    lib().oracle_collide_srt2(fp, gp, float(tau), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def collide_trt2(f, g, tau, magic):
+    f, fp = _d(f)
+    g, gp = _d(g)
+    out = np.zeros(27)
+    lib().oracle_collide_trt2(fp, gp, float(tau), float(magic), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def trt_minus_rate(tau, magic):
+    return float(lib().oracle_trt_minus_rate(float(tau), float(magic)))
+
+
+COLLISIONS = {"chm": 0, "srt2": 1, "trt2": 2}
+
+
 def zouhe(f, axis, sign, is_inlet, u_in=(0.0, 0.0, 0.0), rho_out=1.0):
     f = np.array(f, dtype=np.float64, copy=True)
     u_in, up = _d(u_in)
@@ -173,7 +210,8 @@ class Case:
 
     def __init__(self, mask, periodic=(0, 0, 0), links=None, inlet_center=(0.0, 0.0, 0.0),
                  inlet_radius=1.0, tau=0.6, omega_hi=(1.0, 1.0, 1.0, 1.0), g0=(0.0, 0.0, 0.0),
-                 gamp=(0.0, 0.0, 0.0), gomega=0.0, rho_out=1.0, tau_cell=None):
+                 gamp=(0.0, 0.0, 0.0), gomega=0.0, rho_out=1.0, tau_cell=None, collision="chm",
+                 trt_magic=3.0 / 16.0):
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         assert mask.ndim == 3
         self.shape = mask.shape
@@ -203,6 +241,8 @@ class Case:
         if not h:
             raise ValueError("oracle_create: " + err.value.decode())
         self._h = h
+        if lib().oracle_set_collision(h, COLLISIONS[collision], float(trt_magic)) != 0:
+            raise ValueError("bad collision model or magic parameter")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -346,6 +346,88 @@ double oracle_waveform(const double* a, const double* b, int nh, double P, doubl
 }
 
 /* ------------------------------------------------------------------------------------------
+ * The classical operators the paper compares against (Sec. 2.1.2): the single-relaxation-time
+ * (SRT, BGK) operator with the second-order equilibrium, and the two-relaxation-time (TRT)
+ * operator it cites as the fix for the viscosity-dependent wall position of bounce-back.  The
+ * paper prints neither; the readings are the textbook forms.
+ *   Second-order equilibrium: the Hermite expansion of Eq. (EDF) truncated after the
+ *   second-order term, f_eq2_i = w_i rho [1 + c_i.u/c_s^2 + (c_i.u)^2/(2 c_s^4) - u.u/(2 c_s^2)].
+ *   Body force (as for the CHM-MRT operator: u = sum c f / rho + g/2, F = rho g): the
+ *   second-order force term of Guo, Zheng and Shi (2002),
+ *     F_i = w_i [ (c_i - u)/c_s^2 + (c_i.u) c_i / c_s^4 ] . F,
+ *   whose odd part is w_i c_i.F / c_s^2 and whose even part is the rest.
+ *   SRT:  f* = f + (f_eq2 - f)/tau + (1 - 1/(2 tau)) F_i.
+ *   TRT (Ginzburg): even / odd parts p_i = (f_i + f_opp(i))/2, m_i = (f_i - f_opp(i))/2 relax with
+ *     w+ = 1/tau and w- = 1/(Lambda/(tau - 1/2) + 1/2), Lambda the "magic" parameter;
+ *     f* = f - w+ (p - p_eq) - w- (m - m_eq) + (1 - w+/2) F_even + (1 - w-/2) F_odd.
+ *   Lambda = (tau - 1/2)^2 gives w- = w+ and the SRT operator.
+ * ------------------------------------------------------------------------------------------ */
+void oracle_feq2(double rho, const double u[3], double* feq)
+{
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < NQ; ++i) {
+        double cu = 0.0;
+        for (int d = 0; d < 3; ++d) cu += cvel(i, d) * u[d];
+        feq[i] = weight(i) * rho * (1.0 + cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+    }
+}
+
+/* Guo force term split into its even and odd parts (both without the (1 - w/2) factor). */
+static void guo_force(const double u[3], const double F[3], double* Feven, double* Fodd)
+{
+    for (int i = 0; i < NQ; ++i) {
+        double cu = 0.0, cF = 0.0, uF = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            cu += cvel(i, d) * u[d];
+            cF += cvel(i, d) * F[d];
+            uF += u[d] * F[d];
+        }
+        Fodd[i] = weight(i) * cF / CS2;
+        Feven[i] = weight(i) * (-uF / CS2 + cu * cF / (CS2 * CS2));
+    }
+}
+
+static void moments_rho_u(const double* f, const double g[3], double* rho, double u[3])
+{
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < NQ; ++i) {
+        r += f[i];
+        for (int d = 0; d < 3; ++d) j[d] += cvel(i, d) * f[i];
+    }
+    *rho = r;
+    for (int d = 0; d < 3; ++d) u[d] = j[d] / r + 0.5 * g[d];
+}
+
+void oracle_collide_srt2(const double* f, const double g[3], double tau, double* fout)
+{
+    double rho, u[3], feq[NQ], Fe[NQ], Fo[NQ];
+    moments_rho_u(f, g, &rho, u);
+    const double F[3] = {rho * g[0], rho * g[1], rho * g[2]};
+    oracle_feq2(rho, u, feq);
+    guo_force(u, F, Fe, Fo);
+    const double w = 1.0 / tau;
+    for (int i = 0; i < NQ; ++i) fout[i] = f[i] + w * (feq[i] - f[i]) + (1.0 - 0.5 * w) * (Fe[i] + Fo[i]);
+}
+
+double oracle_trt_minus_rate(double tau, double magic) { return 1.0 / (magic / (tau - 0.5) + 0.5); }
+
+void oracle_collide_trt2(const double* f, const double g[3], double tau, double magic, double* fout)
+{
+    double rho, u[3], feq[NQ], Fe[NQ], Fo[NQ];
+    moments_rho_u(f, g, &rho, u);
+    const double F[3] = {rho * g[0], rho * g[1], rho * g[2]};
+    oracle_feq2(rho, u, feq);
+    guo_force(u, F, Fe, Fo);
+    const double wp = 1.0 / tau, wm = oracle_trt_minus_rate(tau, magic);
+    for (int i = 0; i < NQ; ++i) {
+        const int o = opposite(i);
+        const double p = 0.5 * (f[i] + f[o]), m = 0.5 * (f[i] - f[o]);
+        const double peq = 0.5 * (feq[i] + feq[o]), meq = 0.5 * (feq[i] - feq[o]);
+        fout[i] = f[i] - wp * (p - peq) - wm * (m - meq) + (1.0 - 0.5 * wp) * Fe[i] + (1.0 - 0.5 * wm) * Fo[i];
+    }
+}
+
+/* ------------------------------------------------------------------------------------------
  * A whole case on a voxel box (Sec. 2.1.1 LBE; Sec. 2.1.4 walls; Sec. 2.2 boundaries).
  *   mask (x fastest): 0 solid, 1 fluid, 2 inlet, 3 outlet.  Cells outside a non-periodic face
  *   count as solid.  Inlet/outlet cells lie on exactly one non-periodic box face, whose inward
@@ -375,6 +457,8 @@ typedef struct {
     double g0[3], gamp[3], gomega, rho_out;
     double wa[16], wb[16], wP, wpeak;
     int wnh, has_wave;
+    int collision;    /* 0 CHM-MRT, 1 SRT with f_eq2, 2 TRT with f_eq2 */
+    double tau, magic;
     int64_t n;
 } oracle_case;
 
@@ -542,6 +626,9 @@ oracle_case* oracle_create(int nx, int ny, int nz, const uint8_t* mask, const in
     }
     oracle_rates(tau, omega_hi, C->s);
     for (int k = 0; k < 4; ++k) C->omega_hi[k] = omega_hi[k];
+    C->tau = tau;
+    C->collision = 0;
+    C->magic = 3.0 / 16.0;
     /* an optional relaxation time per cell (a viscosity field, e.g. an absorbing layer before an
      * outlet); the second-order rate of the cell is then 1/tau_cell */
     if (tau_box) {
@@ -568,6 +655,16 @@ oracle_case* oracle_create(int nx, int ny, int nz, const uint8_t* mask, const in
     stream(C);
     apply_open_boundaries(C, 0);
     return C;
+}
+
+/* Collision operator of the case: 0 CHM-MRT (default), 1 SRT with the second-order
+ * equilibrium, 2 TRT with the second-order equilibrium and magic parameter `magic`. */
+int oracle_set_collision(oracle_case* C, int model, double magic)
+{
+    if (model < 0 || model > 2 || !(magic > 0.0)) return 1;
+    C->collision = model;
+    C->magic = magic;
+    return 0;
 }
 
 int oracle_set_waveform(oracle_case* C, const double* a, const double* b, int nh, double period,
@@ -626,7 +723,11 @@ void oracle_step(oracle_case* C, int64_t nsteps)
         gforce(C, C->n, g);
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < nf; ++k) {
-            if (C->tau_cell) {
+            if (C->collision != 0) {
+                const double tk = C->tau_cell ? C->tau_cell[k] : C->tau;
+                if (C->collision == 1) oracle_collide_srt2(C->f + k * NQ, g, tk, C->fpost + k * NQ);
+                else oracle_collide_trt2(C->f + k * NQ, g, tk, C->magic, C->fpost + k * NQ);
+            } else if (C->tau_cell) {
                 double sk[NQ];
                 oracle_rates(C->tau_cell[k], C->omega_hi, sk);
                 oracle_collide(C->f + k * NQ, g, sk, C->fpost + k * NQ);
