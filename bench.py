@@ -15,8 +15,10 @@ copy bandwidth achieved with the algorithmic 27 reads + 27 writes per update (21
 
 Arms:
   default            the CUDA library (this repository), FP32 storage as the headline, FP16 and
-                     BF16 storage as variants; plus an end-to-end figure through the public API
-                     with host buffers, and the FP64 oracle timed on the host cores.
+                     BF16 storage, the A-B scheme and the classical SRT and TRT operators
+                     (second-order equilibrium) as variants; plus an end-to-end figure through
+                     the public API with host buffers, and the FP64 oracle timed on the host
+                     cores.
   --impl reference   the FP64 CPU oracle alone on the same workload (bounded sample: the
                      one-layer z-slab, exact for this z-invariant flow), on the host cores.
 Multi-GPU (torchrun): each rank runs an independent replica of the workload (weak scaling);
@@ -293,11 +295,14 @@ def main():
 
     results = {}
     clocks = None
-    variants = [("fp32", "esoteric")] if args.no_variants else [
-        ("fp32", "esoteric"), ("fp16", "esoteric"), ("bf16", "esoteric"), ("fp32", "ab")]
-    for storage, scheme in variants:
+    variants = [("fp32", "esoteric", "chm")] if args.no_variants else [
+        ("fp32", "esoteric", "chm"), ("fp16", "esoteric", "chm"), ("bf16", "esoteric", "chm"), ("fp32", "ab", "chm"),
+        ("fp32", "esoteric", "srt2"), ("fp32", "esoteric", "trt2")]
+    for storage, scheme, collision in variants:
         key = storage if scheme == "esoteric" else f"{storage}_{scheme}"
-        dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme)
+        if collision != "chm":
+            key += "_" + collision
+        dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme, collision=collision)
         best, tune = dom.autotune(20)
         info = dom.info()
         nf = info["n_fluid"]
@@ -321,7 +326,7 @@ def main():
         bytes_alg = 2 * 27 * BYTES_PER_VALUE[storage] * nf
         results[key] = {"ms_per_step": ms, "mlups": nf / (ms * 1e-3) / 1e6, "fluid_cells": nf,
                         "algorithmic_bytes_per_launch": bytes_alg,
-                        "achieved_gbs": bytes_alg / (ms * 1e-3) / 1e9, "scheme": scheme,
+                        "achieved_gbs": bytes_alg / (ms * 1e-3) / 1e9, "scheme": scheme, "collision": collision,
                         "launch_config": lbm.LAUNCH_CONFIG_NAMES[best],
                         "autotune_ms_back_to_back": {k: round(v, 5) for k, v in tune.items()},
                         "device_bytes": info["device_bytes"], "slots": info["n_slots"]}

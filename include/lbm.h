@@ -63,6 +63,17 @@ typedef enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1, LBM_STORE_BF16 = 2 } lbm_
  *     x + {0,1}^3 (plus a small side buffer at Bouzidi cells). */
 typedef enum { LBM_SCHEME_AB = 0, LBM_SCHEME_ESOTERIC = 1 } lbm_scheme;
 
+/* Collision operator.
+ *   CHM_MRT: the paper's operator (Sec. 2.1.3): central Hermite moments, full-expansion
+ *     equilibrium, second-order rate 1/tau, third- to sixth-order rates omega_hi.
+ *   SRT2: the classical single-relaxation-time operator with the second-order equilibrium that
+ *     the paper compares against (Sec. 2.1.2), f* = f + (f_eq2 - f)/tau + (1 - 1/(2 tau)) F_i,
+ *     F_i the second-order (Guo) force term.
+ *   TRT2: the two-relaxation-time operator (Sec. 2.1.2) with the same equilibrium and force
+ *     term: even parts relax with 1/tau, odd parts with 1/(trt_magic/(tau - 1/2) + 1/2).
+ * The inlet/outlet closures and wall rules are the same for all three. */
+typedef enum { LBM_COLLISION_CHM_MRT = 0, LBM_COLLISION_SRT2 = 1, LBM_COLLISION_TRT2 = 2 } lbm_collision;
+
 /* Physical parameters (Sec. 2.1.3: S is diagonal in central Hermite moment space). */
 typedef struct {
     double tau;          /* relaxation time of the six second-order moments: rate 1/tau,
@@ -76,6 +87,9 @@ typedef struct {
     int32_t periodic[3]; /* nonzero: the axis wraps (its extent must be a multiple of 4) */
     int32_t storage;     /* lbm_storage */
     int32_t scheme;      /* lbm_scheme; default ESOTERIC */
+    int32_t collision;   /* lbm_collision; default CHM_MRT */
+    double trt_magic;    /* TRT2 only: Lambda = (tau - 1/2)(1/w- - 1/2) > 0; default 3/16 (halfway
+                            bounce-back then places a plane wall exactly half-way, any tau) */
 } lbm_params;
 
 /* Device memory callbacks: return a device pointer aligned to 256 bytes, or NULL. */
@@ -223,8 +237,8 @@ lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_conf
  * graph and replayed (the per-step force and inflow of every domain are uploaded by the graph's
  * first node).  Results are bit-identical to stepping each domain alone.
  *   lbm_batch_create: doms[n] (1..4096 distinct domains, esoteric twist, one storage precision,
- *     all or none with unit higher-order rates) stay owned by the caller and must outlive the
- *     batch; graph_steps in 1..4096.  The batch runs (and captures) its work on a private
+ *     one collision operator, and for CHM-MRT all or none with unit higher-order rates) stay
+ *     owned by the caller and must outlive the batch; graph_steps in 1..4096.  The batch runs (and captures) its work on a private
  *     non-blocking stream, ordered by events after the work already enqueued on cuda_stream
  *     (NULL: legacy default) and on each domain's stream, and before anything enqueued there
  *     later.  Small tables are allocated through doms[0]'s allocator.  Errors: INVALID_ARG, OOM,

@@ -36,6 +36,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -475,6 +476,93 @@ __device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a)
     for (int k = 0; k < 9; ++k) inv3(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, ux2 + CS2);
 }
 
+// The classical operators the paper compares against (Sec. 2.1.2), with the second-order
+// equilibrium f_eq2_i = w_i rho [1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u] and the second-order (Guo)
+// force term F_i = w_i [3 (c - u) + 9 (c.u) c] . F, F = rho g, u = j / rho + g / 2.
+// TRT: the even and odd parts of each pair (i, opp(i)) relax with a.s2 and a.wm; the even and
+// odd parts of F_i are scaled by (1 - s2/2) and (1 - wm/2).  SRT2 is the case wm = s2.
+// Deviation form throughout: with d = f - w, f_eq2 - w = w [(rho - 1) + rho (3 c.u + 4.5 (c.u)^2
+// - 1.5 u.u)], so the O(1) weights never enter a rounding.  The FP32 weights are not exact:
+// sum_i w_i and sum_i 3 w_i c_i c_i differ from 1 and the identity by ~3e-8, so relaxing toward
+// f_eq2 would create mass omega * 3e-8 * (rho - 1) and momentum omega * 3e-8 * rho u every step
+// (a systematic drift that grows with time, unlike rounding).  The post-collision mass and
+// momentum are therefore restored to their exact values rho and j + F: mass through the rest
+// population, momentum through the three face pairs (each pair's difference carries one axis
+// and leaves the mass unchanged).
+template <bool TRT>
+__device__ __forceinline__ void collide_trt2(float (&d)[Q], const LevelArgs& a)
+{
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += d[i];
+        if (cx_of(i)) jx += cx_of(i) > 0 ? d[i] : -d[i];
+        if (cy_of(i)) jy += cy_of(i) > 0 ? d[i] : -d[i];
+        if (cz_of(i)) jz += cz_of(i) > 0 ? d[i] : -d[i];
+    }
+    const float rho = 1.0f + drho, ir = 1.0f / rho;
+    const float ux = fmaf(jx, ir, 0.5f * a.g[0]), uy = fmaf(jy, ir, 0.5f * a.g[1]), uz = fmaf(jz, ir, 0.5f * a.g[2]);
+    const float Fx = rho * a.g[0], Fy = rho * a.g[1], Fz = rho * a.g[2];
+    const float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
+    const float wp = a.s2, wm = TRT ? a.wm : a.s2;
+    const float kp = 1.0f - 0.5f * wp, km = 1.0f - 0.5f * wm;
+    {  // rest population: even only
+        constexpr float w = w_of(13);
+        const float peq = w * (drho - rho * uu15);
+        d[13] = d[13] - wp * (d[13] - peq) - kp * w * uF3;
+    }
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        const int o = Q - 1 - i;
+        const float w = w_of(i);
+        const float cu = (float)cx_of(i) * ux + (float)cy_of(i) * uy + (float)cz_of(i) * uz;
+        const float cF = (float)cx_of(i) * Fx + (float)cy_of(i) * Fy + (float)cz_of(i) * Fz;
+        const float peq = w * (drho + rho * (4.5f * cu * cu - uu15));
+        const float meq = w * rho * 3.0f * cu;
+        const float Fe = w * (9.0f * cu * cF - uF3), Fo = w * 3.0f * cF;
+        const float p = 0.5f * (d[i] + d[o]), m = 0.5f * (d[i] - d[o]);
+        const float ev = kp * Fe - wp * (p - peq), od = km * Fo - wm * (m - meq);
+        d[i] = d[i] + ev + od;
+        d[o] = d[o] + ev - od;
+    }
+    float pm = 0.0f, px = 0.0f, py = 0.0f, pz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        pm += d[i];
+        if (cx_of(i)) px += cx_of(i) > 0 ? d[i] : -d[i];
+        if (cy_of(i)) py += cy_of(i) > 0 ? d[i] : -d[i];
+        if (cz_of(i)) pz += cz_of(i) > 0 ? d[i] : -d[i];
+    }
+    // face pairs (-x, +x) = (12, 14), (-y, +y) = (10, 16), (-z, +z) = (4, 22)
+    const float hx = 0.5f * ((jx + Fx) - px), hy = 0.5f * ((jy + Fy) - py), hz = 0.5f * ((jz + Fz) - pz);
+    d[14] += hx;
+    d[12] -= hx;
+    d[16] += hy;
+    d[10] -= hy;
+    d[22] += hz;
+    d[4] -= hz;
+    d[13] += drho - pm;
+}
+
+template <int COLL>
+__device__ __forceinline__ void collide_model(float (&d)[Q], const LevelArgs& a)
+{
+    if (COLL == COLL_CHM_FAST) collide_fast(d, a);
+    else if (COLL == COLL_CHM) collide(d, a);
+    else collide_trt2<COLL == COLL_TRT2>(d, a);
+}
+
+// A cell's own second-order rate s2 (an absorbing layer): SRT2 relaxes both parities with it,
+// TRT2 derives its odd rate from it through Lambda.
+template <int COLL>
+__device__ __forceinline__ void set_own_rate(LevelArgs& la, float s2)
+{
+    la.s2 = s2;
+    if (COLL == COLL_SRT2) la.wm = s2;
+    if (COLL == COLL_TRT2) la.wm = 1.0f / (la.magic / (1.0f / s2 - 0.5f) + 0.5f);
+}
+
 // ------------------------------------------------------------------------------ gather (read-only)
 // Populations of level n of one fluid cell, for the export and diagnostics kernels.
 template <int ST, int SCHEME>
@@ -496,7 +584,7 @@ __device__ __forceinline__ void gather(const DomainView& v, const void* src, uin
 // ------------------------------------------------------------------------------ kernels
 // One fused update of the cell at `slot` (a lane of a warp that covers half of one brick; all
 // 32 lanes must call it together: the neighbour row goes round by shuffle).
-template <int ST, int SCHEME, bool FAST>
+template <int ST, int SCHEME, int COLL>
 __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, void* dst, const LevelArgs& a,
                                           uint32_t slot, uint32_t lane)
 {
@@ -507,7 +595,7 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
     const uint32_t n = (uint32_t)v.n_slots;
     float d[Q];
     LevelArgs la = a;
-    if (word & WORD_OWN_TAU) la.s2 = __ldg(v.s2_cell + slot);
+    if (word & WORD_OWN_TAU) set_own_rate<COLL>(la, __ldg(v.s2_cell + slot));
     if (SCHEME == LBM_SCHEME_ESOTERIC) {
         const int32_t row = __ldg(v.nb8 + brick * 8u + (lane & 7u));
         uint32_t cs[8];
@@ -515,8 +603,7 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         if (!fluid) return;
         fetch_et<ST, true>(dst, n, cs, wm, a.parity, d);
         const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
-        if (FAST) collide_fast(d, la);
-        else collide(d, la);
+        collide_model<COLL>(d, la);
         store_et<ST>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t rec = (uint32_t)v.aux[slot];
@@ -530,21 +617,20 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
         if (!fluid) return;
         if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
-        if (FAST) collide_fast(d, la);
-        else collide(d, la);
+        collide_model<COLL>(d, la);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
     }
 }
 
-template <int ST, int SCHEME, int BRICKS, int MINB, bool FAST>
+template <int ST, int SCHEME, int BRICKS, int MINB, int COLL>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step(DomainView v, const void* src, void* dst, LevelArgs a)
 {
     const uint32_t slot = blockIdx.x * (uint32_t)(BRICKS * BRICK_CELLS) + threadIdx.x;
     // the active slots are a multiple of 64, so this exit is taken by whole warps
     if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
-    step_cell<ST, SCHEME, FAST>(v, src, dst, a, slot, threadIdx.x & 31u);
+    step_cell<ST, SCHEME, COLL>(v, src, dst, a, slot, threadIdx.x & 31u);
 }
 
 // Software-pipelined persistent variant of the FP32 esoteric-twist step.  Each CTA walks over
@@ -562,7 +648,7 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-template <int BRICKS, int MINB, bool FAST>
+template <int BRICKS, int MINB, int COLL>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step_et_pipe(DomainView v, float* __restrict__ pop, LevelArgs a)
 {
@@ -606,13 +692,12 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
             if (word & WORD_FLUID) {
                 const uint32_t wm = word & WORD_WALL_MASK;
                 LevelArgs la = a;
-                if (word & WORD_OWN_TAU) la.s2 = __ldg(v.s2_cell + slot);
+                if (word & WORD_OWN_TAU) set_own_rate<COLL>(la, __ldg(v.s2_cell + slot));
                 float d[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) d[i] = stage[(st * Q + i) * T + tid];
                 const uint32_t half = wm ? wall_rules<LBM_STORE_FP32, LBM_SCHEME_ESOTERIC>(v, nullptr, slot, word, a, d) : 0u;
-                if (FAST) collide_fast(d, la);
-                else collide(d, la);
+                collide_model<COLL>(d, la);
                 store_et<LBM_STORE_FP32>(pop, n, cs, a.parity, d);
                 if (half) {
                     const uint32_t rec = (uint32_t)v.aux[slot];
@@ -631,7 +716,7 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
 // Several domains (esoteric twist, one storage precision) in one launch: the CTAs run over the
 // concatenated brick lists; each warp finds its domain by binary search in the brick prefix
 // sums and updates one of that domain's half-bricks with the domain's own level arguments.
-template <int ST, int BRICKS, int MINB, bool FAST>
+template <int ST, int BRICKS, int MINB, int COLL>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step_batch(const BatchEntry* __restrict__ ent, const int64_t* __restrict__ brick_start, int n_dom,
                  const LevelArgs* __restrict__ args)
@@ -648,7 +733,7 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     const DomainView v = ent[lo].view;
     const LevelArgs a = args[lo];
     const uint32_t slot = (uint32_t)((gbrick - __ldg(brick_start + lo)) * BRICK_CELLS) + (threadIdx.x & 63u);
-    step_cell<ST, LBM_SCHEME_ESOTERIC, FAST>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
+    step_cell<ST, LBM_SCHEME_ESOTERIC, COLL>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
 }
 
 template <int ST, int SCHEME>
@@ -851,6 +936,18 @@ __global__ void __launch_bounds__(DIAG_THREADS)
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
+// Calls f(std::integral_constant<int, COLL>{}) for the collision kernel `coll`.
+template <class F>
+cudaError_t with_coll(int coll, F&& f)
+{
+    switch (coll) {
+    case COLL_CHM: return f(std::integral_constant<int, COLL_CHM>{});
+    case COLL_CHM_FAST: return f(std::integral_constant<int, COLL_CHM_FAST>{});
+    case COLL_SRT2: return f(std::integral_constant<int, COLL_SRT2>{});
+    default: return f(std::integral_constant<int, COLL_TRT2>{});
+    }
+}
+
 // ------------------------------------------------------------------------------ launchers
 // Launch configurations of the step kernel: (bricks per CTA, minimum resident CTAs per SM);
 // the second number sets the register budget, 65536 / (threads * CTAs).
@@ -859,11 +956,10 @@ cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const
 {
     if (v.n_bricks == 0) return cudaSuccess;
     const int grid = grid_for(v.n_bricks, BRICKS);
-    if (a.fast_rates)
-        k_step<ST, SCHEME, BRICKS, MINB, true><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
-    else
-        k_step<ST, SCHEME, BRICKS, MINB, false><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
-    return cudaGetLastError();
+    return with_coll(a.coll, [&](auto c) {
+        k_step<ST, SCHEME, BRICKS, MINB, decltype(c)::value><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+        return cudaGetLastError();
+    });
 }
 
 template <int BRICKS, int MINB>
@@ -872,21 +968,18 @@ cudaError_t launch_step_et_pipe(const DomainView& v, void* pop, const LevelArgs&
     if (v.n_bricks == 0) return cudaSuccess;
     constexpr int T = BRICKS * BRICK_CELLS;
     const size_t smem = sizeof(float) * 2 * Q * T;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step_et_pipe<BRICKS, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_step_et_pipe<BRICKS, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t n_chunks = (v.n_bricks + BRICKS - 1) / BRICKS;
     const int grid = (int)std::min<int64_t>(n_chunks, (int64_t)sms * MINB);
-    if (a.fast_rates)
-        k_step_et_pipe<BRICKS, MINB, true><<<grid, T, smem, s>>>(v, static_cast<float*>(pop), a);
-    else
-        k_step_et_pipe<BRICKS, MINB, false><<<grid, T, smem, s>>>(v, static_cast<float*>(pop), a);
-    return cudaGetLastError();
+    return with_coll(a.coll, [&](auto c) {
+        auto k = k_step_et_pipe<BRICKS, MINB, decltype(c)::value>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, T, smem, s>>>(v, static_cast<float*>(pop), a);
+        return cudaGetLastError();
+    });
 }
 
 template <int ST, int SCHEME>
@@ -973,27 +1066,27 @@ cudaError_t launch_apply_du(int scheme, const DomainView& v, void* pop, int pari
 
 template <int ST, int BRICKS, int MINB>
 cudaError_t launch_step_batch_t(const BatchEntry* ent, const int64_t* brick_start, int n_dom, int64_t total_bricks,
-                                const LevelArgs* args, int fast, cudaStream_t s)
+                                const LevelArgs* args, int coll, cudaStream_t s)
 {
     if (total_bricks == 0) return cudaSuccess;
     const int grid = grid_for(total_bricks, BRICKS);
-    if (fast)
-        k_step_batch<ST, BRICKS, MINB, true><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
-    else
-        k_step_batch<ST, BRICKS, MINB, false><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
-    return cudaGetLastError();
+    return with_coll(coll, [&](auto c) {
+        k_step_batch<ST, BRICKS, MINB, decltype(c)::value><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start,
+                                                                                              n_dom, args);
+        return cudaGetLastError();
+    });
 }
 
 template <int ST>
 cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
-                              int64_t total_bricks, const LevelArgs* args, int fast, cudaStream_t s)
+                              int64_t total_bricks, const LevelArgs* args, int coll, cudaStream_t s)
 {
     switch (config) {
-    case 0: return launch_step_batch_t<ST, 4, 3>(ent, brick_start, n_dom, total_bricks, args, fast, s);
-    case 1: return launch_step_batch_t<ST, 4, 4>(ent, brick_start, n_dom, total_bricks, args, fast, s);
-    case 2: return launch_step_batch_t<ST, 2, 6>(ent, brick_start, n_dom, total_bricks, args, fast, s);
-    case 3: return launch_step_batch_t<ST, 2, 8>(ent, brick_start, n_dom, total_bricks, args, fast, s);
-    default: return launch_step_batch_t<ST, 2, 10>(ent, brick_start, n_dom, total_bricks, args, fast, s);
+    case 0: return launch_step_batch_t<ST, 4, 3>(ent, brick_start, n_dom, total_bricks, args, coll, s);
+    case 1: return launch_step_batch_t<ST, 4, 4>(ent, brick_start, n_dom, total_bricks, args, coll, s);
+    case 2: return launch_step_batch_t<ST, 2, 6>(ent, brick_start, n_dom, total_bricks, args, coll, s);
+    case 3: return launch_step_batch_t<ST, 2, 8>(ent, brick_start, n_dom, total_bricks, args, coll, s);
+    default: return launch_step_batch_t<ST, 2, 10>(ent, brick_start, n_dom, total_bricks, args, coll, s);
     }
 }
 

@@ -121,8 +121,16 @@ struct lbm_domain {
         a.rho_out = (float)params.rho_out;
         a.drho_out = (float)(params.rho_out - 1.0);
         a.parity = (int)(n & 1);
-        a.fast_rates = (params.omega_hi[0] == 1.0 && params.omega_hi[1] == 1.0 && params.omega_hi[2] == 1.0 &&
-                        params.omega_hi[3] == 1.0) ? 1 : 0;
+        const bool fast = params.omega_hi[0] == 1.0 && params.omega_hi[1] == 1.0 && params.omega_hi[2] == 1.0 &&
+                          params.omega_hi[3] == 1.0;
+        a.coll = params.collision == LBM_COLLISION_SRT2   ? COLL_SRT2
+                 : params.collision == LBM_COLLISION_TRT2 ? COLL_TRT2
+                 : fast                                   ? COLL_CHM_FAST
+                                                          : COLL_CHM;
+        a.magic = (float)params.trt_magic;
+        a.wm = params.collision == LBM_COLLISION_TRT2
+                   ? (float)(1.0 / (params.trt_magic / (params.tau - 0.5) + 0.5))
+                   : a.s2;
         return a;
     }
 };
@@ -164,6 +172,10 @@ lbm_status check_params(const lbm_params& p)
         if (!std::isfinite(p.force[d]) || !std::isfinite(p.force_amp[d]))
             return fail(LBM_ERR_INVALID_ARG, "non-finite force");
     if (!std::isfinite(p.force_omega)) return fail(LBM_ERR_INVALID_ARG, "non-finite force_omega");
+    if (p.collision < LBM_COLLISION_CHM_MRT || p.collision > LBM_COLLISION_TRT2)
+        return fail(LBM_ERR_INVALID_ARG, "bad collision model");
+    if (p.collision == LBM_COLLISION_TRT2 && !(p.trt_magic > 0.0 && std::isfinite(p.trt_magic)))
+        return fail(LBM_ERR_INVALID_ARG, "trt_magic must be > 0");
     return LBM_OK;
 }
 
@@ -180,6 +192,8 @@ void lbm_default_params(lbm_params* p)
     p->rho_out = 1.0;
     p->storage = LBM_STORE_FP32;
     p->scheme = LBM_SCHEME_ESOTERIC;
+    p->collision = LBM_COLLISION_CHM_MRT;
+    p->trt_magic = 3.0 / 16.0;
 }
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
@@ -888,7 +902,7 @@ void lbm_destroy(lbm_domain* D)
 struct lbm_batch {
     std::vector<lbm_domain*> doms;
     int storage = 0;
-    int fast = 1;
+    int coll = COLL_CHM_FAST;
     int launch_config = DEFAULT_LAUNCH_CONFIG;
     int graph_steps = 0;
     int64_t total_bricks = 0, total_fluid = 0;
@@ -938,7 +952,7 @@ struct lbm_batch {
                                         stream);
         const Launchers& L = launchers(storage);
         for (int k = 0; k < steps && e == cudaSuccess; ++k)
-            e = L.step_batch(config, d_ent, d_start, n(), total_bricks, d_args + (size_t)k * n(), fast, stream);
+            e = L.step_batch(config, d_ent, d_start, n(), total_bricks, d_args + (size_t)k * n(), coll, stream);
         return e;
     }
     cudaError_t capture()
@@ -985,8 +999,10 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
             return fail(LBM_ERR_INVALID_ARG, "batched domains must use the esoteric-twist scheme");
         if (doms[d]->params.storage != doms[0]->params.storage)
             return fail(LBM_ERR_INVALID_ARG, "batched domains must share one storage precision");
-        if (doms[d]->level_args(0).fast_rates != doms[0]->level_args(0).fast_rates)
-            return fail(LBM_ERR_INVALID_ARG, "batched domains must all use, or all not use, unit higher-order rates");
+        if (doms[d]->level_args(0).coll != doms[0]->level_args(0).coll)
+            return fail(LBM_ERR_INVALID_ARG,
+                        "batched domains must share one collision kernel (operator, and for CHM-MRT whether "
+                        "all higher-order rates are 1)");
         for (int e = 0; e < d; ++e)
             if (doms[e] == doms[d]) return fail(LBM_ERR_INVALID_ARG, "a domain appears twice in the batch");
     }
@@ -994,7 +1010,7 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
     if (!B) return fail(LBM_ERR_OOM, "host allocation failed");
     B->doms.assign(doms, doms + n);
     B->storage = doms[0]->params.storage;
-    B->fast = doms[0]->level_args(0).fast_rates;
+    B->coll = doms[0]->level_args(0).coll;
     B->graph_steps = graph_steps;
     B->user_stream = static_cast<cudaStream_t>(cuda_stream);
     B->owner = doms[0];

@@ -68,7 +68,10 @@ struct LevelArgs {
     float rho_out;
     float drho_out;  // rho_out - 1, rounded once from FP64
     int parity;      // n & 1 (esoteric twist)
-    int fast_rates;  // every 3rd..6th-order rate is 1: the step kernel skips those moments
+    int coll;        // collision kernel: COLL_CHM, COLL_CHM_FAST (every 3rd..6th-order rate is
+                     // 1: the step kernel skips those moments), COLL_SRT2, COLL_TRT2
+    float wm;        // SRT2 / TRT2: rate of the odd parts (SRT2: = s2)
+    float magic;     // TRT2: Lambda, for cells with their own tau
 };
 
 // One domain of a batched launch.
@@ -78,6 +81,9 @@ struct BatchEntry {
 };
 
 constexpr int N_LAUNCH_CONFIGS = 6;
+
+// collision kernels (the `coll` of LevelArgs and the COLL template parameter of the step kernels)
+constexpr int COLL_CHM = 0, COLL_CHM_FAST = 1, COLL_SRT2 = 2, COLL_TRT2 = 3;
 constexpr int DEFAULT_LAUNCH_CONFIG = 2;  // 128 threads, 6 CTAs per SM
 
 // Launchers, one set per storage precision (lbm_step_<storage>.cu).  All enqueue on `stream`
@@ -95,7 +101,7 @@ struct Launchers {
                                const int32_t* fl_slot, int64_t n_fluid, double* partials, cudaStream_t stream);
     // twist only: every domain of the batch one step; args[d] are domain d's level arguments
     cudaError_t (*step_batch)(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
-                              int64_t total_bricks, const LevelArgs* args, int fast, cudaStream_t stream);
+                              int64_t total_bricks, const LevelArgs* args, int coll, cudaStream_t stream);
     // learned-corrector velocity shift of the post-collision populations of the previous level
     cudaError_t (*apply_du)(int scheme, const DomainView& v, void* pop, int parity_prev, const int32_t* fl_slot,
                             const int32_t* fl_box, int64_t n_fluid, const float* rho, const float* u, const float* du,

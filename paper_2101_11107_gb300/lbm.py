@@ -30,6 +30,7 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
 N_LAUNCH_CONFIGS = 6
 LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10", "pipe128x6"]
 SCHEME = {"ab": 0, "esoteric": 1}
+COLLISION = {"chm": 0, "srt2": 1, "trt2": 2}
 
 
 class LbmError(RuntimeError):
@@ -42,7 +43,8 @@ class Params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("omega_hi", ctypes.c_double * 4),
                 ("force", ctypes.c_double * 3), ("force_amp", ctypes.c_double * 3),
                 ("force_omega", ctypes.c_double), ("rho_out", ctypes.c_double),
-                ("periodic", ctypes.c_int32 * 3), ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32)]
+                ("periodic", ctypes.c_int32 * 3), ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("collision", ctypes.c_int32), ("trt_magic", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -170,7 +172,7 @@ class Domain:
     def __init__(self, mask, periodic=(0, 0, 0), links=None, inlet_center=None, inlet_radius=0.0,
                  tau=0.6, omega_hi=(1.0, 1.0, 1.0, 1.0), force=(0.0, 0.0, 0.0), force_amp=(0.0, 0.0, 0.0),
                  force_omega=0.0, rho_out=1.0, storage="fp32", scheme="esoteric", tau_cell=None, device=None,
-                 stream=None):
+                 stream=None, collision="chm", trt_magic=3.0 / 16.0):
         import torch
         L = load_library()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -193,6 +195,8 @@ class Domain:
         p.rho_out = rho_out
         p.storage = STORE[storage] if isinstance(storage, str) else int(storage)
         p.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+        p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+        p.trt_magic = trt_magic
         self.storage = storage
         if links is None or len(links[0]) == 0:
             lc = ld = lq = None

@@ -38,6 +38,7 @@ def test_default_params(L):
     p = lbm.Params()
     L.lbm_default_params(ctypes.byref(p))
     assert p.tau == 0.6 and list(p.omega_hi) == [1.0] * 4 and p.rho_out == 1.0 and p.storage == 0
+    assert p.collision == 0 and p.trt_magic == 3.0 / 16.0
 
 
 def _create(L, mask, links=None, params=None, inlet_center=None, inlet_radius=0.0):
@@ -69,7 +70,7 @@ def _create(L, mask, links=None, params=None, inlet_center=None, inlet_radius=0.
 
 @pytest.mark.parametrize("case", ["mask_value", "periodic_extent", "tau", "omega", "link_not_wall",
                                   "link_q", "link_on_inlet", "duplicate_link", "open_cell_off_face",
-                                  "inlet_without_radius"])
+                                  "inlet_without_radius", "collision", "trt_magic"])
 def test_invalid_arguments_rejected_before_device_work(L, case):
     mask = np.ones((4, 8, 8), np.uint8)
     mask[:, :, 0] = 0
@@ -100,6 +101,10 @@ def test_invalid_arguments_rejected_before_device_work(L, case):
     elif case == "inlet_without_radius":
         mask[:, :, 1] = 0
         mask[:, :, 0] = 2
+    elif case == "collision":
+        kw["params"] = {"collision": 3}
+    elif case == "trt_magic":
+        kw["params"] = {"collision": 2, "trt_magic": -1.0}
     if case == "link_on_inlet":
         pass
     st, msg, h = _create(L, mask, **kw)
