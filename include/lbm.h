@@ -311,6 +311,36 @@ lbm_status lbm_apply_velocity_correction(lbm_domain* dom, const float* du, int32
 lbm_status lbm_restrict(const float* fine_rho, const float* fine_u, const uint8_t* fine_mask, int32_t fnx,
                         int32_t fny, int32_t fnz, float* coarse_rho, float* coarse_u, void* cuda_stream);
 
+/*
+ * Flow metrics of the paper's comparisons, on the device.
+ *   lbm_mean_reset / lbm_mean_sample / lbm_mean_get: running means of rho and u (the time
+ *     averaging of Sec. 3.3).  reset allocates (once, through the domain's allocator: 32 bytes per
+ *     fluid cell) and zeroes FP64 sums; sample adds the current level's rho, u of every fluid
+ *     cell (asynchronous, one kernel; call it between lbm_step calls at the sampling interval);
+ *     get writes the means (as lbm_get_macroscopic: dense box or compact fluid list, host or
+ *     device pointers; host pointers wait) and *n_samples (may be NULL).  Errors: INVALID_ARG,
+ *     STATE (sample or get before reset, get without samples), OOM, CUDA.
+ *   lbm_probe: rho, ux, uy, uz of n fluid cells at the current level (monitoring points,
+ *     Sec. 2.2.2), out[p][4]; fluid_index[p] is the position of the cell in the compact fluid
+ *     list (fluid cells in box order, x fastest).  Host pointers: indices are checked
+ *     (INVALID_ARG outside [0, n_fluid)) and the call waits; device pointers: asynchronous, an
+ *     index outside the range yields NaNs.
+ *   lbm_similarity_index: the similarity index of Sec. 3.4 between two velocity fields u_a, u_b
+ *     (device pointers, three planes [3][n] each) over the points with mask[p] != 0 (device
+ *     pointer; NULL: all n points), read with the factor 1/2 that bounds it by 1:
+ *     SI = mean_p 1/2 (1 + cos theta_p) (1 - | |u_a,p|/max|u_a| - |u_b,p|/max|u_b| |), the maxima
+ *     over the same points, cos theta = 0 where either vector is zero, 0 for an empty set.
+ *     FP64 terms and fixed-order reductions (reproducible); a fixed scratch inside the library,
+ *     no allocation; calls are serialised; waits for cuda_stream (NULL: legacy default).
+ *     Errors: INVALID_ARG, CUDA.
+ */
+lbm_status lbm_mean_reset(lbm_domain* dom);
+lbm_status lbm_mean_sample(lbm_domain* dom);
+lbm_status lbm_mean_get(lbm_domain* dom, float* rho, float* u, int32_t dense, int32_t device_ptrs, int64_t* n_samples);
+lbm_status lbm_probe(lbm_domain* dom, const int64_t* fluid_index, int32_t n, float* out, int32_t device_ptrs);
+lbm_status lbm_similarity_index(const float* u_a, const float* u_b, const uint8_t* mask, int64_t n, double* si,
+                                void* cuda_stream);
+
 /* Waits for all work enqueued on the domain. */
 lbm_status lbm_sync(lbm_domain* dom);
 

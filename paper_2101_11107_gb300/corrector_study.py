@@ -50,13 +50,11 @@ def geometry_pairs(seeds, fine_edge, period_f, reynolds, workers):
 
 
 def similarity_index(u_hr, u_lr, mask):
-    """Mean over fluid cells of 1/2 (1 + cos) (1 - | |u_hr|/max|u_hr| - |u_lr|/max|u_lr| |)."""
-    fl = mask > 0
-    a, b = u_hr[:, fl], u_lr[:, fl]
-    na, nb = np.linalg.norm(a, axis=0), np.linalg.norm(b, axis=0)
-    cos = (a * b).sum(0) / np.maximum(na * nb, 1e-30)
-    mag = 1.0 - np.abs(na / max(na.max(), 1e-30) - nb / max(nb.max(), 1e-30))
-    return float(np.mean(0.5 * (1.0 + cos) * mag))
+    """Similarity index of Sec. 3.4 (factor 1/2) over the cells where mask != 0, computed on the
+    device by lbm_similarity_index; u_hr, u_lr CUDA tensors (3, nz, ny, nx), mask a CUDA tensor."""
+    from . import lbm
+
+    return lbm.similarity_index(u_hr, u_lr, mask)
 
 
 def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples_per_period, train_steps, lr,
@@ -199,15 +197,16 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         e_plain, e_corr, e_out, si_plain, si_corr, si_out = [], [], [], [], [], []
         fl = cm > 0
         for a, b in zip(plain, corr):
+            uo_t = a["u"] + net.forward(a["rho"], a["u"], mask=cm_eval, out_mask=bm_eval)
             uf = a["u_fine"].cpu().numpy()
             up = a["u"].cpu().numpy()
             uc = b["u"].cpu().numpy()
-            uo = (a["u"] + net.forward(a["rho"], a["u"], mask=cm_eval, out_mask=bm_eval)).cpu().numpy()
+            uo = uo_t.cpu().numpy()
             for arr, v in ((e_plain, up), (e_corr, uc), (e_out, uo)):
                 arr.append(float(np.linalg.norm((v - uf)[:, fl]) / np.linalg.norm(uf[:, fl])))
-            si_plain.append(similarity_index(uf, up, cm))
-            si_corr.append(similarity_index(uf, uc, cm))
-            si_out.append(similarity_index(uf, uo, cm))
+            si_plain.append(similarity_index(a["u_fine"], a["u"], cm_eval))
+            si_corr.append(similarity_index(a["u_fine"], b["u"], cm_eval))
+            si_out.append(similarity_index(a["u_fine"], uo_t, cm_eval))
         # wall times, no sampling inside
         times = {}
         for name in ("fine", "coarse", "coarse+corrector"):

@@ -736,6 +736,49 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     step_cell<ST, LBM_SCHEME_ESOTERIC, COLL>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
 }
 
+// Running means (the time averaging of Sec. 3.3): sums[k] += (rho, ux, uy, uz) of fluid cell k at
+// the current level, in FP64 so that thousands of samples add without loss.
+template <int ST, int SCHEME>
+__global__ void __launch_bounds__(256)
+    k_mean_sample(DomainView v, const void* src, LevelArgs a, const int32_t* fl_slot, int64_t n_fluid, Sum4* sums)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_fluid) return;
+    const uint32_t slot = (uint32_t)fl_slot[k];
+    float d[Q];
+    gather<ST, SCHEME>(v, src, slot, v.word[slot], a, d);
+    const Moments M = moments(d, a.g);
+    Sum4 s = sums[k];
+    s.x += (double)M.rho;
+    s.y += (double)M.ux;
+    s.z += (double)M.uy;
+    s.w += (double)M.uz;
+    sums[k] = s;
+}
+
+// Monitoring-point probes (Sec. 2.2.2 follows the velocity at points around the sac):
+// out[p] = (rho, ux, uy, uz) of fluid cell idx[p] (fluid index: box order, x fastest); an index
+// outside [0, n_fluid) gives NaNs.
+template <int ST, int SCHEME>
+__global__ void __launch_bounds__(128)
+    k_probe(DomainView v, const void* src, LevelArgs a, const int32_t* fl_slot, int64_t n_fluid, const int64_t* idx,
+            int n, float4* out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t k = idx[p];
+    if (k < 0 || k >= n_fluid) {
+        out[p] = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                             __int_as_float(0x7fc00000));
+        return;
+    }
+    const uint32_t slot = (uint32_t)fl_slot[k];
+    float d[Q];
+    gather<ST, SCHEME>(v, src, slot, v.word[slot], a, d);
+    const Moments M = moments(d, a.g);
+    out[p] = make_float4(M.rho, M.ux, M.uy, M.uz);
+}
+
 template <int ST, int SCHEME>
 __global__ void __launch_bounds__(256)
     k_macroscopic(DomainView v, const void* src, LevelArgs a, const int32_t* fl_slot, const int32_t* fl_box,
@@ -1023,6 +1066,30 @@ cudaError_t launch_macroscopic(int scheme, const DomainView& v, const void* src,
 }
 
 template <int ST>
+cudaError_t launch_mean_sample(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, int64_t n_fluid, Sum4* sums, cudaStream_t s)
+{
+    if (n_fluid == 0) return cudaSuccess;
+    if (scheme == LBM_SCHEME_ESOTERIC)
+        k_mean_sample<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, src, a, fl_slot, n_fluid, sums);
+    else
+        k_mean_sample<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, src, a, fl_slot, n_fluid, sums);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_probe(int scheme, const DomainView& v, const void* src, const LevelArgs& a, const int32_t* fl_slot,
+                         int64_t n_fluid, const int64_t* idx, int n, float4* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (scheme == LBM_SCHEME_ESOTERIC)
+        k_probe<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n, 128), 128, 0, s>>>(v, src, a, fl_slot, n_fluid, idx, n, out);
+    else
+        k_probe<ST, LBM_SCHEME_AB><<<grid_for(n, 128), 128, 0, s>>>(v, src, a, fl_slot, n_fluid, idx, n, out);
+    return cudaGetLastError();
+}
+
+template <int ST>
 cudaError_t launch_init_equilibrium(int scheme, const DomainView& v, void* dst, int parity_prev,
                                     const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid,
                                     const float* rho, const float* u, int64_t n_box, cudaStream_t s)
@@ -1093,8 +1160,9 @@ cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* 
 template <int ST>
 const Launchers& make_launchers()
 {
-    static const Launchers L = {&launch_step<ST>, &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
-                                &launch_diagnostics<ST>, &launch_step_batch<ST>, &launch_apply_du<ST>};
+    static const Launchers L = {&launch_step<ST>,        &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
+                                &launch_diagnostics<ST>, &launch_step_batch<ST>, &launch_apply_du<ST>,
+                                &launch_mean_sample<ST>, &launch_probe<ST>};
     return L;
 }
 

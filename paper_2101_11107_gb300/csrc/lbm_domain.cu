@@ -46,6 +46,8 @@ struct lbm_domain {
     int launch_config = DEFAULT_LAUNCH_CONFIG;
     double* d_partials = nullptr;
     lbm_diagnostics* d_diag = nullptr;
+    Sum4* d_mean = nullptr;  // running-mean sums (rho, ux, uy, uz) per fluid cell, FP64
+    int64_t n_mean = 0;
     int64_t time = 0;
     // inflow waveform, tabulated over one period in FP64 and rounded to FP32
     bool has_wave = false;
@@ -695,6 +697,103 @@ lbm_status lbm_get_macroscopic(lbm_domain* D, float* rho, float* u, int32_t dens
         D->dev_free(stage, bytes);
     }
     if (e != cudaSuccess) return cuda_fail(e, "macroscopic export");
+    return LBM_OK;
+}
+
+lbm_status lbm_mean_reset(lbm_domain* D)
+{
+    g_last_error.clear();
+    if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
+    const size_t bytes = sizeof(Sum4) * (size_t)std::max<int64_t>(D->n_fluid, 1);
+    if (!D->d_mean) {
+        D->d_mean = static_cast<Sum4*>(D->dev_alloc(bytes));
+        if (!D->d_mean) return fail(LBM_ERR_OOM, "allocation failed: running means");
+    }
+    cudaError_t e = cudaMemsetAsync(D->d_mean, 0, bytes, D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the running means");
+    D->n_mean = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_mean_sample(lbm_domain* D)
+{
+    g_last_error.clear();
+    if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
+    if (!D->d_mean) return fail(LBM_ERR_STATE, "lbm_mean_reset was not called");
+    const LevelArgs a = D->level_args(D->time);
+    cudaError_t e = launchers(D->params.storage)
+                        .mean_sample(D->params.scheme, D->view, D->src(), a, D->d_fl_slot, D->n_fluid, D->d_mean,
+                                     D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "running-mean sample");
+    ++D->n_mean;
+    return LBM_OK;
+}
+
+lbm_status lbm_mean_get(lbm_domain* D, float* rho, float* u, int32_t dense, int32_t device_ptrs, int64_t* n_samples)
+{
+    g_last_error.clear();
+    if (!D || !rho || !u) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    if (!D->d_mean || D->n_mean == 0) return fail(LBM_ERR_STATE, "no samples since lbm_mean_reset");
+    if (n_samples) *n_samples = D->n_mean;
+    const int64_t n_out = dense ? (int64_t)D->nx * D->ny * D->nz : D->n_fluid;
+    float* dr = rho;
+    float* du = u;
+    float* stage = nullptr;
+    const size_t bytes = sizeof(float) * 4 * (size_t)std::max<int64_t>(n_out, 1);
+    if (!device_ptrs) {
+        stage = static_cast<float*>(D->dev_alloc(bytes));
+        if (!stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+        dr = stage;
+        du = stage + n_out;
+    }
+    cudaError_t e = cudaSuccess;
+    if (dense) e = cudaMemsetAsync(dr, 0, sizeof(float) * n_out, D->stream);
+    if (dense && e == cudaSuccess) e = cudaMemsetAsync(du, 0, sizeof(float) * 3 * n_out, D->stream);
+    if (e == cudaSuccess) e = launch_mean_out(D->d_mean, D->d_fl_box, D->n_fluid, D->n_mean, dense, dr, du, n_out, D->stream);
+    if (stage) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, sizeof(float) * n_out, cudaMemcpyDeviceToHost, D->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, sizeof(float) * 3 * n_out, cudaMemcpyDeviceToHost, D->stream);
+        cudaError_t e2 = cudaStreamSynchronize(D->stream);
+        if (e == cudaSuccess) e = e2;
+        D->dev_free(stage, bytes);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "running-mean export");
+    return LBM_OK;
+}
+
+lbm_status lbm_probe(lbm_domain* D, const int64_t* fluid_index, int32_t n, float* out, int32_t device_ptrs)
+{
+    g_last_error.clear();
+    if (!D || n < 0 || (n > 0 && (!fluid_index || !out))) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return LBM_OK;
+    if (!device_ptrs)
+        for (int32_t p = 0; p < n; ++p)
+            if (fluid_index[p] < 0 || fluid_index[p] >= D->n_fluid)
+                return fail(LBM_ERR_INVALID_ARG, "probe index outside [0, n_fluid)");
+    const LevelArgs a = D->level_args(D->time);
+    const int64_t* di = fluid_index;
+    float4* dout = reinterpret_cast<float4*>(out);
+    void* stage = nullptr;
+    const size_t bytes = (sizeof(int64_t) + sizeof(float4)) * (size_t)n;
+    cudaError_t e = cudaSuccess;
+    if (!device_ptrs) {
+        stage = D->dev_alloc(bytes);
+        if (!stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+        dout = static_cast<float4*>(stage);
+        di = reinterpret_cast<const int64_t*>(static_cast<char*>(stage) + sizeof(float4) * (size_t)n);
+        e = cudaMemcpyAsync(const_cast<int64_t*>(di), fluid_index, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice,
+                            D->stream);
+    }
+    if (e == cudaSuccess)
+        e = launchers(D->params.storage)
+                .probe(D->params.scheme, D->view, D->src(), a, D->d_fl_slot, D->n_fluid, di, n, dout, D->stream);
+    if (stage) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToHost, D->stream);
+        cudaError_t e2 = cudaStreamSynchronize(D->stream);
+        if (e == cudaSuccess) e = e2;
+        D->dev_free(stage, bytes);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "probe");
     return LBM_OK;
 }
 

@@ -60,6 +60,11 @@ struct DomainView {
     int64_t n_io;
 };
 
+// FP64 running sums of (rho, ux, uy, uz) of one fluid cell.
+struct alignas(32) Sum4 {
+    double x, y, z, w;
+};
+
 // Per-launch arguments of a time level n.
 struct LevelArgs {
     float g[3];    // body acceleration g(n)
@@ -106,7 +111,15 @@ struct Launchers {
     cudaError_t (*apply_du)(int scheme, const DomainView& v, void* pop, int parity_prev, const int32_t* fl_slot,
                             const int32_t* fl_box, int64_t n_fluid, const float* rho, const float* u, const float* du,
                             int64_t n_box, cudaStream_t stream);
+    // running-mean accumulation (FP64 sums of rho, u per fluid cell) and point probes
+    cudaError_t (*mean_sample)(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
+                               const int32_t* fl_slot, int64_t n_fluid, Sum4* sums, cudaStream_t stream);
+    cudaError_t (*probe)(int scheme, const DomainView& v, const void* src, const LevelArgs& a, const int32_t* fl_slot,
+                         int64_t n_fluid, const int64_t* idx, int n, float4* out, cudaStream_t stream);
 };
+// storage-independent output of the running means (lbm_metrics.cu)
+cudaError_t launch_mean_out(const Sum4* sums, const int32_t* fl_box, int64_t n_fluid, int64_t n_samples, int dense,
+                            float* rho, float* u, int64_t n_out, cudaStream_t stream);
 const Launchers& launchers_fp32();
 const Launchers& launchers_fp16();
 const Launchers& launchers_bf16();

@@ -26,7 +26,8 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_batch_destroy", "lbm_corrector_num_params",
            "lbm_corrector_create", "lbm_corrector_get_params", "lbm_corrector_set_params", "lbm_corrector_forward",
            "lbm_corrector_gradients", "lbm_corrector_train_step", "lbm_corrector_apply", "lbm_corrector_destroy",
-           "lbm_apply_velocity_correction", "lbm_restrict"]
+           "lbm_apply_velocity_correction", "lbm_restrict", "lbm_mean_reset", "lbm_mean_sample", "lbm_mean_get",
+           "lbm_probe", "lbm_similarity_index"]
 N_LAUNCH_CONFIGS = 6
 LAUNCH_CONFIG_NAMES = ["256x3", "256x4", "128x6", "128x8", "128x10", "pipe128x6"]
 SCHEME = {"ab": 0, "esoteric": 1}
@@ -121,13 +122,19 @@ def load_library(path: str = LIB_PATH):
     L.lbm_corrector_destroy.restype = None
     L.lbm_apply_velocity_correction.argtypes = [vp, vp, i32]
     L.lbm_restrict.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
+    L.lbm_mean_reset.argtypes = [vp]
+    L.lbm_mean_sample.argtypes = [vp]
+    L.lbm_mean_get.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(i64)]
+    L.lbm_probe.argtypes = [vp, vp, i32, vp, i32]
+    L.lbm_similarity_index.argtypes = [vp, vp, vp, i64, ctypes.POINTER(dbl), vp]
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
                  "lbm_get_macroscopic", "lbm_get_diagnostics", "lbm_get_info", "lbm_sync",
                  "lbm_save_state", "lbm_load_state", "lbm_set_launch_config", "lbm_autotune",
                  "lbm_get_diagnostics_noalloc", "lbm_batch_create", "lbm_batch_step",
-                 "lbm_batch_set_launch_config", "lbm_batch_autotune"]:
+                 "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_mean_reset", "lbm_mean_sample",
+                 "lbm_mean_get", "lbm_probe", "lbm_similarity_index"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -179,6 +186,7 @@ class Domain:
         if mask.ndim != 3:
             raise ValueError("mask must have shape (nz, ny, nx)")
         self.shape = mask.shape
+        self._mask = mask
         nz, ny, nx = mask.shape
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
@@ -290,6 +298,45 @@ class Domain:
         _check(load_library().lbm_get_macroscopic(self._h, ctypes.c_void_p(rho.data_ptr()),
                                                   ctypes.c_void_p(u.data_ptr()), int(dense), 1))
 
+    # ---------------------------------------------------------------- flow metrics
+    def mean_reset(self):
+        _check(load_library().lbm_mean_reset(self._h))
+
+    def mean_sample(self):
+        _check(load_library().lbm_mean_sample(self._h))
+
+    def mean(self, dense=True):
+        """(rho_mean, u_mean, n_samples) as numpy float32 arrays, shaped as macroscopic()."""
+        nz, ny, nx = self.shape
+        n = nx * ny * nz if dense else self.info()["n_fluid"]
+        rho = np.empty(n, np.float32)
+        u = np.empty(3 * n, np.float32)
+        ns = ctypes.c_int64()
+        _check(load_library().lbm_mean_get(self._h, _ptr(rho), _ptr(u), int(dense), 0, ctypes.byref(ns)))
+        if dense:
+            return rho.reshape(nz, ny, nx), u.reshape(3, nz, ny, nx), ns.value
+        return rho, u.reshape(3, n), ns.value
+
+    def fluid_index(self, points):
+        """Positions in the compact fluid list of box cells given as (z, y, x) triples."""
+        if not hasattr(self, "_fluid_rank"):
+            fl = self._mask.reshape(-1) != 0
+            rank = np.cumsum(fl) - 1
+            self._fluid_rank = np.where(fl, rank, -1)
+        nz, ny, nx = self.shape
+        pts = np.asarray(points, dtype=np.int64).reshape(-1, 3)
+        idx = self._fluid_rank[(pts[:, 0] * ny + pts[:, 1]) * nx + pts[:, 2]]
+        if np.any(idx < 0):
+            raise ValueError("probe point is not a fluid cell")
+        return idx.astype(np.int64)
+
+    def probe(self, points):
+        """(n, 4) float32 array of (rho, ux, uy, uz) at box cells given as (z, y, x) triples."""
+        idx = np.ascontiguousarray(self.fluid_index(points))
+        out = np.empty((len(idx), 4), np.float32)
+        _check(load_library().lbm_probe(self._h, _ptr(idx), len(idx), _ptr(out), 0))
+        return out
+
     def diagnostics(self, raise_unstable=True) -> dict:
         dg = Diagnostics()
         st = load_library().lbm_get_diagnostics(self._h, ctypes.byref(dg))
@@ -343,6 +390,26 @@ class Domain:
 
     def load_state(self, path):
         _check(load_library().lbm_load_state(self._h, os.fsencode(path)))
+
+
+def similarity_index(u_a, u_b, mask=None, stream=None) -> float:
+    """lbm_similarity_index on CUDA tensors u_a, u_b of shape (3, ...) (float32) and an optional
+    uint8 mask of shape (...): the similarity index of Sec. 3.4 (factor 1/2, bounded by 1)."""
+    import torch
+    ua = u_a.to(torch.float32).contiguous()
+    ub = u_b.to(torch.float32).contiguous()
+    n = ua[0].numel()
+    if ub[0].numel() != n or ua.shape[0] != 3 or ub.shape[0] != 3:
+        raise ValueError("u_a and u_b must have shape (3, ...) with the same number of points")
+    m = None if mask is None else mask.to(torch.uint8).contiguous()
+    if m is not None and m.numel() != n:
+        raise ValueError("mask must have one entry per point")
+    st = torch.cuda.current_stream(ua.device) if stream is None else stream
+    out = ctypes.c_double()
+    _check(load_library().lbm_similarity_index(ctypes.c_void_p(ua.data_ptr()), ctypes.c_void_p(ub.data_ptr()),
+                                                None if m is None else ctypes.c_void_p(m.data_ptr()), n,
+                                                ctypes.byref(out), ctypes.c_void_p(st.cuda_stream)))
+    return out.value
 
 
 def flatten_params(params):
