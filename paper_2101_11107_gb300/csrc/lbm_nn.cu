@@ -13,13 +13,15 @@
 //   * Only 4^3 tiles that hold fluid, dilated by one tile, are evaluated (the rest of the box
 //     stays zero): the receptive field of the three layers is 3 cells, so outputs at fluid cells
 //     equal those of the dense network.
-//   * Convolution = implicit GEMM on the tensor cores with warp-level mma.sync m16n8k16 (BF16 in,
-//     FP32 accumulate): a CTA per tile, a warp per 4x4 z-slice (M = 16 cells), N = 16 output
-//     channels (two n8 tiles), K = 27 offsets x 16 input channels; the CTA's weights sit in
-//     shared memory.  The data-gradient is the same kernel with the flipped, transposed kernel
-//     and a ReLU gate; the weight-gradient is a GEMM over cells (M = 16 output channels,
-//     N = 16 input channels, K = cells) with per-CTA register accumulation and one FP32 atomic
-//     per weight per CTA.
+//   * Convolution = implicit GEMM on the 5th-generation tensor cores (k_conv_tc): tcgen05.mma
+//     with the accumulator in tensor memory, operands staged in shared memory by TMA, a CTA per
+//     8 x 16 x 1 slab (M = 128 cells, N = 16 output channels, K = 27 offsets x 16 input
+//     channels).  The data-gradient is the same kernel with the flipped, transposed kernel and
+//     a ReLU gate.  The weight-gradient is a GEMM over cells with M = 16 output channels, below
+//     the smallest tcgen05 tile (M = 64): it stays on warp-level mma.sync m16n8k16 (BF16 in,
+//     FP32 accumulate) with per-CTA register accumulation and one FP32 atomic per weight per
+//     CTA.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -60,74 +62,167 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// out[p][co] = act(sum_o sum_ci w[o][co][ci] in[p + o][ci] + bias[co]), zeroed where gate <= 0.
-// OUT_F32: write channels 0..3 as FP32 to a dense unpadded [cells][4] array; else BF16 padded.
+// ------------------------------------------------------------------------------ tcgen05 conv
+// out[p][co] = act(sum_o sum_ci w[o][co][ci] in[p + o][ci] + bias[co]), zeroed where gate <= 0,
+// as an implicit GEMM on the 5th-generation tensor cores.  A CTA of 128 threads computes one
+// slab of 8 (x) x 16 (y) x 1 (z) cells: M = 128 rows (cell x + 8 y), N = 16 output channels,
+// K = 27 offsets x 16 input channels, i.e. 27 tcgen05.mma (kind::f16, BF16 in, FP32 accumulator
+// of 128 lanes x 16 columns in tensor memory) issued by one thread.
+//   * The slab's halo (10 x 18 x 3 cells) comes in by two TMA tile loads of the channels-last
+//     padded activations (a 4-D tensor map, box 8 channels x 10 x 18 x 3), one per group of 8
+//     channels, so shared memory holds two "planes" of 16 bytes per cell.  For offset o the A
+//     operand is a K-major, non-swizzled canonical layout read straight out of those planes:
+//     8-row core matrices are 8 consecutive cells along x (16 B apart), core matrices along M
+//     are the 16 y rows (160 B apart), and the two K core matrices are the two planes.  No
+//     gather, no copy: the 27 descriptors differ only in their start address.
+//   * B (the 27 weight blocks, N x K = 16 x 16) is staged once per CTA in the same canonical
+//     layout (core matrix (n-group, k-group) at 128-byte steps).
+//   * The epilogue reads each row back with tcgen05.ld (warp w owns lanes 32w..32w+31), adds the
+//     bias, applies ReLU and the gate, and writes 32 bytes per cell.
+// Every wait (TMA, MMA completion) is bounded; on a timeout the CTA flags the error, waits for
+// what it issued, frees its tensor memory and returns.
+constexpr int SL_X = 8, SL_Y = 16;                      // slab = M = 128 cells
+constexpr int HX = SL_X + 2, HY = SL_Y + 2, HZ = 3;     // halo
+constexpr uint32_t PLANE_BYTES = HX * HY * HZ * 16;     // 8640: one TMA box
+constexpr uint32_t PLANE_STRIDE = 8704;                 // 128-byte aligned plane step
+constexpr uint32_t W_OFF = 2 * PLANE_STRIDE;            // weights after the two planes
+constexpr uint32_t CONV_SMEM = W_OFF + 27 * 512;        // 31232 B
+constexpr int TC_WAIT_LIMIT = 1 << 22;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128, N = 16
+constexpr uint32_t CONV_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
+{
+    for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done)
+                     : "r"(su32(bar)), "r"(phase)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <bool OUT_F32>
 __global__ void __launch_bounds__(128)
-    k_conv(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
-           int relu, const __nv_bfloat16* __restrict__ gate, void* __restrict__ out, const int4* __restrict__ tiles, Box b)
+    k_conv_tc(const __grid_constant__ CUtensorMap tin, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
+              int relu, const __nv_bfloat16* __restrict__ gate, void* __restrict__ out, const int4* __restrict__ slabs,
+              Box b, unsigned int* __restrict__ err)
 {
-    __shared__ __align__(16) __nv_bfloat16 sw[NW];
-    for (int t = threadIdx.x; t < NW / 8; t += blockDim.x)
-        reinterpret_cast<uint4*>(sw)[t] = __ldg(reinterpret_cast<const uint4*>(w) + t);
-    __syncthreads();
-    const int4 tile = tiles[blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int z = tile.z + warp;
-    const int xa = tile.x + (g & 3), ya = tile.y + (g >> 2);  // A rows g and g + 8
-    const int yb = ya + 2;
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    const uint32_t* in32 = reinterpret_cast<const uint32_t*>(in);
-    const uint32_t* sw32 = reinterpret_cast<const uint32_t*>(sw);
-#pragma unroll 3
-    for (int o = 0; o < 27; ++o) {
-        const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-        const size_t ca = pidx(b, xa + dx, ya + dy, z + dz) * CH / 2, cb = pidx(b, xa + dx, yb + dy, z + dz) * CH / 2;
-        uint32_t a[4];
-        a[0] = __ldg(in32 + ca + t);
-        a[1] = __ldg(in32 + cb + t);
-        a[2] = __ldg(in32 + ca + t + 4);
-        a[3] = __ldg(in32 + cb + t + 4);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            uint32_t bb[2];
-            bb[0] = sw32[(o * CH * CH + (8 * j + g) * CH) / 2 + t];
-            bb[1] = sw32[(o * CH * CH + (8 * j + g) * CH) / 2 + t + 4];
-            mma16816(acc[j], a, bb);
-        }
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 sl = slabs[blockIdx.x];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_tma)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_mma)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(su32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {  // halo: padded coordinates (x0, y0, z) .. + (9, 17, 2), channels 0-7 and 8-15
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bar_tma)),
+                     "r"(2u * PLANE_BYTES)
+                     : "memory");
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < 2; ++j)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4, %5}], [%6];" ::"r"(su32(smem + j * PLANE_STRIDE)),
+                "l"(reinterpret_cast<uint64_t>(&tin)), "r"(8 * j), "r"(sl.x), "r"(sl.y), "r"(sl.z), "r"(su32(&bar_tma))
+                : "memory");
+    }
+    // weights: chunk (o, co, j) = w[o][co][8j..8j+7] -> core matrix (co / 8, j) of block o
+    for (int q = tid; q < 27 * 16 * 2; q += 128) {
+        const int o = q >> 5, co = (q >> 1) & 15, j = q & 1;
+        *reinterpret_cast<uint4*>(smem + W_OFF + o * 512 + (2 * (co >> 3) + j) * 128 + (co & 7) * 16) =
+            __ldg(reinterpret_cast<const uint4*>(w) + q);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights visible to the tensor cores
+    const bool halo_ok = __syncthreads_and(tc_wait(&bar_tma, 0)) != 0;  // one decision for the CTA
+    const uint32_t tbase = tmem_base;
+    if (halo_ok && tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = su32(smem), w0 = su32(smem + W_OFF);
+#pragma unroll 1
+        for (int o = 0; o < 27; ++o) {
+            const uint32_t ox = o % 3, oy = (o / 3) % 3, oz = o / 9;
+            const uint64_t ad = smem_desc(a0 + 16u * ((oz * HY + oy) * HX + ox), PLANE_STRIDE, HX * 16);
+            const uint64_t bd = smem_desc(w0 + 512u * (uint32_t)o, 128, 256);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tbase),
+                "l"(ad), "l"(bd), "r"(CONV_IDESC), "r"((uint32_t)(o > 0))
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&bar_mma))
+                     : "memory");
+    }
+    const bool mma_ok = halo_ok && __syncthreads_and(tc_wait(&bar_mma, 0)) != 0;
+    if (mma_ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tbase + ((uint32_t)(warp * 32) << 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int m = warp * 32 + lane;
+        const int x = sl.x + (m & 7), y = sl.y + (m >> 3), z = sl.z;
+        if (x < b.nx && y < b.ny) {
+            float v[CH];
+            const size_t pc = pidx(b, x, y, z);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int co = 8 * j + 2 * t;
-            const int y = h ? yb : ya;
-            float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
-            if (bias) {
-                v0 += bias[co];
-                v1 += bias[co + 1];
-            }
-            if (relu) {
-                v0 = fmaxf(v0, 0.0f);
-                v1 = fmaxf(v1, 0.0f);
-            }
-            const size_t pc = pidx(b, xa, y, z);
-            if (gate) {
-                if (!(__bfloat162float(gate[pc * CH + co]) > 0.0f)) v0 = 0.0f;
-                if (!(__bfloat162float(gate[pc * CH + co + 1]) > 0.0f)) v1 = 0.0f;
+            for (int co = 0; co < CH; ++co) {
+                float t = __uint_as_float(r[co]);
+                if (bias) t += __ldg(bias + co);
+                if (relu) t = fmaxf(t, 0.0f);
+                if (gate && !(__bfloat162float(gate[pc * CH + co]) > 0.0f)) t = 0.0f;
+                v[co] = t;
             }
             if (OUT_F32) {
-                if (co < 4) {
-                    float* o4 = static_cast<float*>(out) + (((size_t)z * b.ny + y) * b.nx + xa) * 4;
-                    o4[co] = v0;
-                    o4[co + 1] = v1;
-                }
+                *reinterpret_cast<float4*>(static_cast<float*>(out) + (((size_t)z * b.ny + y) * b.nx + x) * 4) =
+                    make_float4(v[0], v[1], v[2], v[3]);
             } else {
-                __nv_bfloat162 v = __floats2bfloat162_rn(v0, v1);
-                *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(out) + pc * CH + co) = v;
+                uint32_t pk[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                    pk[k] = *reinterpret_cast<const uint32_t*>(&h);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + pc * CH);
+                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
+    } else {
+        if (tid == 0) atomicOr(err, 1u);
+        // wait (bounded) for what is still in flight before the tensor memory is freed
+        if (!halo_ok) tc_wait(&bar_tma, 0);
+        else tc_wait(&bar_mma, 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tbase) : "memory");
 }
 
 // dW[o][co][ci] += sum_p dy[p][co] x[p + o][ci] and db[co] += sum_p dy[p][co] over the tiles;
@@ -351,6 +446,31 @@ __global__ void k_restrict(const float* __restrict__ frho, const float* __restri
 
 int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+// 4-D tensor map over a channels-last padded activation buffer [pz][py][px][16] (BF16) whose
+// box is one slab halo of one 8-channel group: 8 channels x 10 x 18 x 3 cells.
+cudaError_t encode_halo_map(CUtensorMap* tm, const void* base, const Box& b)
+{
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)b.px, (cuuint64_t)b.py, (cuuint64_t)b.pz};
+    const cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)b.px * CH * 2, (cuuint64_t)b.px * b.py * CH * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)HZ};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 namespace lbm {
@@ -372,7 +492,12 @@ struct lbm_corrector {
     void* ctx = nullptr;
     std::vector<void*> owned;
     uint8_t* mask = nullptr;
-    int4* tiles = nullptr;
+    int4* tiles = nullptr;   // 4^3 tiles with fluid, dilated by one tile (weight gradients)
+    int4* slabs = nullptr;   // 8 x 16 x 1 slabs covering those tiles (convolutions)
+    int64_t n_slabs = 0;
+    unsigned int* err = nullptr;  // set by a conv CTA whose bounded wait gave up
+    CUtensorMap tmaps[5];         // halo maps of x0, y1, y2, dO, dy2 (the convolutions' inputs)
+    const void* tmap_of[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     __nv_bfloat16 *x0 = nullptr, *y1 = nullptr, *y2 = nullptr, *dO = nullptr, *dy = nullptr, *dy2 = nullptr;
     float* o4 = nullptr;
     float *rho = nullptr, *u = nullptr, *du = nullptr;  // staging on the coarse box
@@ -408,10 +533,23 @@ struct lbm_corrector {
     cudaError_t conv(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, int relu,
                      const __nv_bfloat16* gate, void* out, bool f32)
     {
-        if (n_tiles == 0) return cudaSuccess;
-        if (f32) k_conv<true><<<(int)n_tiles, 128, 0, stream>>>(in, w, bias, relu, gate, out, tiles, box);
-        else k_conv<false><<<(int)n_tiles, 128, 0, stream>>>(in, w, bias, relu, gate, out, tiles, box);
+        if (n_slabs == 0) return cudaSuccess;
+        int t = 0;
+        while (t < 5 && tmap_of[t] != in) ++t;
+        if (t == 5) return cudaErrorInvalidValue;
+        if (f32)
+            k_conv_tc<true><<<(int)n_slabs, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, box, err);
+        else
+            k_conv_tc<false><<<(int)n_slabs, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, box, err);
         return cudaGetLastError();
+    }
+    // nonzero device error word (read after the stream has been synchronised)
+    bool device_error()
+    {
+        unsigned int h = 0;
+        if (cudaMemcpy(&h, err, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+        if (h) cudaMemset(err, 0, sizeof(h));
+        return h != 0;
     }
     cudaError_t forward(const uint8_t* cmask, const float* r, const float* uu)
     {
@@ -503,9 +641,24 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
                             if (X < 0 || Y < 0 || Z < 0 || X >= tx || Y >= ty || Z >= tz) continue;
                             near = has[(size_t)X + (size_t)tx * ((size_t)Y + (size_t)ty * (size_t)Z)] != 0;
                         }
-                if (near) tl.push_back(make_int4(4 * x, 4 * y, 4 * z, 0));
+                if (near) {
+                    tl.push_back(make_int4(4 * x, 4 * y, 4 * z, 0));
+                    use[(size_t)x + (size_t)tx * ((size_t)y + (size_t)ty * (size_t)z)] = 1;
+                }
             }
     K->n_tiles = (int64_t)tl.size();
+    // slabs of 8 x 16 x 1 cells that meet a tile of that set
+    std::vector<int4> sv;
+    for (int z = 0; z < nz; ++z)
+        for (int y0 = 0; y0 < ny; y0 += SL_Y)
+            for (int x0 = 0; x0 < nx; x0 += SL_X) {
+                bool any = false;
+                for (int y = y0; y < std::min(ny, y0 + SL_Y) && !any; y += 4)
+                    for (int x = x0; x < std::min(nx, x0 + SL_X) && !any; x += 4)
+                        any = use[(size_t)(x / 4) + (size_t)tx * ((size_t)(y / 4) + (size_t)ty * (size_t)(z / 4))] != 0;
+                if (any) sv.push_back(make_int4(x0, y0, z, 0));
+            }
+    K->n_slabs = (int64_t)sv.size();
     const size_t act = (size_t)K->box.px * K->box.py * K->box.pz * CH * sizeof(__nv_bfloat16);
     const size_t cells = (size_t)K->n_cells;
     bool ok = true;
@@ -516,6 +669,8 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
     };
     K->mask = static_cast<uint8_t*>(D(cells));
     K->tiles = static_cast<int4*>(D(sizeof(int4) * std::max<size_t>(tl.size(), 1)));
+    K->slabs = static_cast<int4*>(D(sizeof(int4) * std::max<size_t>(sv.size(), 1)));
+    K->err = static_cast<unsigned int*>(D(sizeof(unsigned int)));
     K->x0 = static_cast<__nv_bfloat16*>(D(act));
     K->y1 = static_cast<__nv_bfloat16*>(D(act));
     K->y2 = static_cast<__nv_bfloat16*>(D(act));
@@ -542,6 +697,16 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
     cudaError_t e = cudaMemcpyAsync(K->mask, mask, cells, cudaMemcpyHostToDevice, K->stream);
     if (e == cudaSuccess && !tl.empty())
         e = cudaMemcpyAsync(K->tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, K->stream);
+    if (e == cudaSuccess && !sv.empty())
+        e = cudaMemcpyAsync(K->slabs, sv.data(), sizeof(int4) * sv.size(), cudaMemcpyHostToDevice, K->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(K->err, 0, sizeof(unsigned int), K->stream);
+    {
+        const __nv_bfloat16* ins[5] = {K->x0, K->y1, K->y2, K->dO, K->dy2};
+        for (int t = 0; t < 5 && e == cudaSuccess; ++t) {
+            e = encode_halo_map(&K->tmaps[t], ins[t], K->box);
+            K->tmap_of[t] = ins[t];
+        }
+    }
     for (__nv_bfloat16* p : {K->x0, K->y1, K->y2, K->dO, K->dy, K->dy2})
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, act, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->o4, 0, sizeof(float) * 4 * cells, K->stream);
@@ -608,6 +773,7 @@ lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, K->count, sizeof(cnt), cudaMemcpyDeviceToHost, K->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(K->stream);
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector gradients: ") + cudaGetErrorString(e));
+    if (K->device_error()) return nn_fail(LBM_ERR_TIMEOUT, "a convolution gave up waiting for its copies or MMAs");
     *loss = cnt ? l / (3.0 * (double)cnt) : 0.0;
     return LBM_OK;
 }
@@ -634,6 +800,8 @@ lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(&cnt, K->count, sizeof(cnt), cudaMemcpyDeviceToHost, K->stream);
     if (e == cudaSuccess && loss) e = cudaStreamSynchronize(K->stream);
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector train step: ") + cudaGetErrorString(e));
+    if (loss && K->device_error())
+        return nn_fail(LBM_ERR_TIMEOUT, "a convolution gave up waiting for its copies or MMAs");
     if (loss) *loss = cnt ? l / (3.0 * (double)cnt) : 0.0;
     return LBM_OK;
 }
