@@ -2,9 +2,13 @@
 
     python -m paper_2101_11107_gb300.run_case womersley fp32 4 [esoteric|ab] [launch config name]
     python -m paper_2101_11107_gb300.run_case aneurysm256 fp16 10
+    python -m paper_2101_11107_gb300.run_case corrector128 fp32 50
 
 Workloads: womersley (64x64x256 pulsatile pipe, radius 28), poiseuille (32x32x64 pipe,
-radius 12), aneurysm256 / aneurysm512 (seeded synthetic aneurysm, seed 11).
+radius 12), aneurysm256 / aneurysm512 (seeded synthetic aneurysm, seed 11); corrector<edge>: the
+learned corrector's forward pass (features, three convolutions, output) on the seed-200
+synthetic aneurysm at that edge after 100 solver steps, repeated `steps` times (initial
+parameters of seed 0), with its CUDA-event time per pass.
 """
 import sys
 
@@ -21,6 +25,26 @@ def main(argv=None):
     from . import lbm
 
     lib_build.build()
+    if case.startswith("corrector"):
+        import torch
+
+        edge = int(case[len("corrector"):] or 128)
+        g = I.aneurysm(200, edge=edge, period=2000.0 * edge / 128.0)
+        net = lbm.Corrector(g.mask, I.corrector_init_params(0), 0.05, 0.01, 0.005)
+        dom = lbm.Domain.from_geometry(g)
+        dom.step(100)
+        rho, u = dom.macroscopic_tensors()
+        for _ in range(3):
+            net.forward(rho, u)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            net.forward(rho, u)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"ok {case} fluid={g.nfluid} forward_ms={e0.elapsed_time(e1) / max(steps, 1):.4f}")
+        return
     if case == "womersley":
         g = I.womersley_pipe()
     elif case == "poiseuille":
