@@ -216,8 +216,8 @@ lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
 /* Number of launch configurations of the fused step kernel. */
 #define LBM_N_LAUNCH_CONFIGS 6
 
-/* Selects the step kernel's launch configuration: 0, 1 = 256 threads (four 4^3 bricks) per CTA
- * with a register budget for 3 or 4 resident CTAs per SM; 2, 3, 4 = 128 threads with 6, 8 or
+/* Selects the step kernel's launch configuration: 0 = 256 threads (four 4^3 bricks) per CTA
+ * with a register budget for 3 resident CTAs per SM; 1, 2, 3, 4 = 128 threads with 7, 6, 8 or
  * 10; 5 = a persistent, software-pipelined variant (128 threads, 6 CTAs per SM; the next cell's
  * populations are copied into shared memory asynchronously while the current one is computed;
  * FP32 esoteric twist only, other domains use 3).  Results do not depend on it.  Default 2.

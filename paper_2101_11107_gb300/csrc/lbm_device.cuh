@@ -1035,7 +1035,7 @@ cudaError_t launch_step_scheme(int config, const DomainView& v, const void* src,
     }
     switch (config) {
     case 0: return launch_step_t<ST, SCHEME, 4, 3>(v, src, dst, a, s);
-    case 1: return launch_step_t<ST, SCHEME, 4, 4>(v, src, dst, a, s);
+    case 1: return launch_step_t<ST, SCHEME, 2, 7>(v, src, dst, a, s);
     case 2: return launch_step_t<ST, SCHEME, 2, 6>(v, src, dst, a, s);
     case 3: return launch_step_t<ST, SCHEME, 2, 8>(v, src, dst, a, s);
     default: return launch_step_t<ST, SCHEME, 2, 10>(v, src, dst, a, s);
@@ -1150,7 +1150,7 @@ cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* 
 {
     switch (config) {
     case 0: return launch_step_batch_t<ST, 4, 3>(ent, brick_start, n_dom, total_bricks, args, coll, s);
-    case 1: return launch_step_batch_t<ST, 4, 4>(ent, brick_start, n_dom, total_bricks, args, coll, s);
+    case 1: return launch_step_batch_t<ST, 2, 7>(ent, brick_start, n_dom, total_bricks, args, coll, s);
     case 2: return launch_step_batch_t<ST, 2, 6>(ent, brick_start, n_dom, total_bricks, args, coll, s);
     case 3: return launch_step_batch_t<ST, 2, 8>(ent, brick_start, n_dom, total_bricks, args, coll, s);
     default: return launch_step_batch_t<ST, 2, 10>(ent, brick_start, n_dom, total_bricks, args, coll, s);
