@@ -214,13 +214,16 @@ lbm_status lbm_get_diagnostics_noalloc(lbm_domain* dom, lbm_diagnostics* out);
 lbm_status lbm_get_info(const lbm_domain* dom, lbm_info* out);
 
 /* Number of launch configurations of the fused step kernel. */
-#define LBM_N_LAUNCH_CONFIGS 6
+#define LBM_N_LAUNCH_CONFIGS 8
 
 /* Selects the step kernel's launch configuration: 0 = 256 threads (four 4^3 bricks) per CTA
  * with a register budget for 3 resident CTAs per SM; 1, 2, 3, 4 = 128 threads with 7, 6, 8 or
  * 10; 5 = a persistent, software-pipelined variant (128 threads, 6 CTAs per SM; the next cell's
  * populations are copied into shared memory asynchronously while the current one is computed;
- * FP32 esoteric twist only, other domains use 3).  Results do not depend on it.  Default 2.
+ * FP32 esoteric twist only, other domains use 3); 6, 7 = two cells per thread (128 threads = four
+ * bricks per CTA, 4 or 3 CTAs per SM; the two cells' collisions as packed FP32x2 arithmetic;
+ * esoteric twist with CHM-MRT at unit higher-order rates only, other domains use 2).  Results
+ * do not depend on it.  Default 2.
  * Errors: INVALID_ARG. */
 lbm_status lbm_set_launch_config(lbm_domain* dom, int32_t config);
 

@@ -403,78 +403,136 @@ __device__ __forceinline__ void collide(float (&d)[Q], const LevelArgs& a)
 //   a_200 = P_xx - 2 u_x j_x + (u_x^2 - c_s^2)(rho - 1),
 //   a_110 = P_xy - u_x j_y - u_y j_x + u_x u_y (rho - 1),
 // and the inverse transform is unchanged.  Same arithmetic as `collide` up to rounding order.
-__device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a)
+// Lane arithmetic of the fast collision: one cell (float) or two cells at once (float2, packed
+// FP32x2 instructions of sm_100+).  Every operation is an explicit round-to-nearest add,
+// multiply or fused multiply-add, and the two forms apply them in the same order, so a cell
+// gives bit-identical results whichever form updates it.
+struct Lane1 {
+    using V = float;
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ V neg(V a) { return -a; }
+    static __device__ __forceinline__ V splat(float s) { return s; }
+    static __device__ __forceinline__ V rcp1p(V drho) { return 1.0f / (1.0f + drho); }
+    static __device__ __forceinline__ V one_plus(V x) { return __fadd_rn(1.0f, x); }
+};
+struct Lane2 {
+    using V = float2;
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
+    static __device__ __forceinline__ V splat(float s) { return make_float2(s, s); }
+    static __device__ __forceinline__ V rcp1p(V drho)
+    {
+        return make_float2(1.0f / (1.0f + drho.x), 1.0f / (1.0f + drho.y));
+    }
+    static __device__ __forceinline__ V one_plus(V x) { return __fadd2_rn(make_float2(1.0f, 1.0f), x); }
+};
+
+template <class L>
+__device__ __forceinline__ void inv3_t(typename L::V& m0, typename L::V& m1, typename L::V& m2, typename L::V u,
+                                       typename L::V u2pcs, typename L::V two_u)
 {
-    float S0[9], S1[9], S2[9];
+    using V = typename L::V;
+    const V S1 = L::fma(u, m0, m1);
+    const V S2 = L::fma(u2pcs, m0, L::fma(two_u, m1, m2));
+    const V g0 = L::sub(m0, S2);
+    m0 = L::mul(L::splat(0.5f), L::sub(S2, S1));
+    m2 = L::mul(L::splat(0.5f), L::add(S2, S1));
+    m1 = g0;
+}
+
+template <class L>
+__device__ __forceinline__ void collide_fast_t(typename L::V (&d)[Q], typename L::V s2, const float g[3])
+{
+    using V = typename L::V;
+    V S0[9], S1[9], S2[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        S2[k] = d[3 * k] + d[3 * k + 2];
-        S0[k] = S2[k] + d[3 * k + 1];
-        S1[k] = d[3 * k + 2] - d[3 * k];
+        S2[k] = L::add(d[3 * k], d[3 * k + 2]);
+        S0[k] = L::add(S2[k], d[3 * k + 1]);
+        S1[k] = L::sub(d[3 * k + 2], d[3 * k]);
     }
-    float T0[3], T1[3], T2[3], U0[3], U1[3], V[3];
+    V T0[3], T1[3], T2[3], U0[3], U1[3], W[3];
 #pragma unroll
     for (int z = 0; z < 3; ++z) {
-        T2[z] = S0[3 * z] + S0[3 * z + 2];
-        T0[z] = T2[z] + S0[3 * z + 1];
-        T1[z] = S0[3 * z + 2] - S0[3 * z];
-        U0[z] = S1[3 * z] + S1[3 * z + 1] + S1[3 * z + 2];
-        U1[z] = S1[3 * z + 2] - S1[3 * z];
-        V[z] = S2[3 * z] + S2[3 * z + 1] + S2[3 * z + 2];
+        T2[z] = L::add(S0[3 * z], S0[3 * z + 2]);
+        T0[z] = L::add(T2[z], S0[3 * z + 1]);
+        T1[z] = L::sub(S0[3 * z + 2], S0[3 * z]);
+        U0[z] = L::add(L::add(S1[3 * z], S1[3 * z + 1]), S1[3 * z + 2]);
+        U1[z] = L::sub(S1[3 * z + 2], S1[3 * z]);
+        W[z] = L::add(L::add(S2[3 * z], S2[3 * z + 1]), S2[3 * z + 2]);
     }
-    const float drho = T0[0] + T0[1] + T0[2];
-    const float jz = T0[2] - T0[0];
-    const float Pzz = T0[2] + T0[0];
-    const float jy = T1[0] + T1[1] + T1[2];
-    const float Pyz = T1[2] - T1[0];
-    const float Pyy = T2[0] + T2[1] + T2[2];
-    const float jx = U0[0] + U0[1] + U0[2];
-    const float Pxz = U0[2] - U0[0];
-    const float Pxy = U1[0] + U1[1] + U1[2];
-    const float Pxx = V[0] + V[1] + V[2];
-    const float rho = 1.0f + drho;
-    const float ir = 1.0f / rho;
-    const float ux = fmaf(jx, ir, 0.5f * a.g[0]);
-    const float uy = fmaf(jy, ir, 0.5f * a.g[1]);
-    const float uz = fmaf(jz, ir, 0.5f * a.g[2]);
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-    const float s2 = a.s2, k2 = 1.0f - a.s2;
-    // central second moments of d, relaxed: b = (1 - s2) a_d - s2 a_w
-    const float a200 = Pxx - 2.0f * ux * jx + (ux2 - CS2) * drho;
-    const float a020 = Pyy - 2.0f * uy * jy + (uy2 - CS2) * drho;
-    const float a002 = Pzz - 2.0f * uz * jz + (uz2 - CS2) * drho;
-    const float a110 = Pxy - ux * jy - uy * jx + ux * uy * drho;
-    const float a101 = Pxz - ux * jz - uz * jx + ux * uz * drho;
-    const float a011 = Pyz - uy * jz - uz * jy + uy * uz * drho;
-    const float ex[3] = {1.0f, -ux, ux2}, ey[3] = {1.0f, -uy, uy2}, ez[3] = {1.0f, -uz, uz2};
+    const V drho = L::add(L::add(T0[0], T0[1]), T0[2]);
+    const V jz = L::sub(T0[2], T0[0]);
+    const V Pzz = L::add(T0[2], T0[0]);
+    const V jy = L::add(L::add(T1[0], T1[1]), T1[2]);
+    const V Pyz = L::sub(T1[2], T1[0]);
+    const V Pyy = L::add(L::add(T2[0], T2[1]), T2[2]);
+    const V jx = L::add(L::add(U0[0], U0[1]), U0[2]);
+    const V Pxz = L::sub(U0[2], U0[0]);
+    const V Pxy = L::add(L::add(U1[0], U1[1]), U1[2]);
+    const V Pxx = L::add(L::add(W[0], W[1]), W[2]);
+    const V rho = L::one_plus(drho);
+    const V ir = L::rcp1p(drho);
+    const V ux = L::fma(jx, ir, L::splat(0.5f * g[0]));
+    const V uy = L::fma(jy, ir, L::splat(0.5f * g[1]));
+    const V uz = L::fma(jz, ir, L::splat(0.5f * g[2]));
+    const V ux2 = L::mul(ux, ux), uy2 = L::mul(uy, uy), uz2 = L::mul(uz, uz);
+    const V uxy = L::mul(ux, uy), uxz = L::mul(ux, uz), uyz = L::mul(uy, uz);
+    const V k2 = L::sub(L::splat(1.0f), s2), ns2 = L::neg(s2);
+    const V mcs = L::splat(-CS2);
+    // central second moments of d (deviation form)
+    const V a200 = L::fma(L::add(ux2, mcs), drho, L::fma(L::mul(L::splat(-2.0f), ux), jx, Pxx));
+    const V a020 = L::fma(L::add(uy2, mcs), drho, L::fma(L::mul(L::splat(-2.0f), uy), jy, Pyy));
+    const V a002 = L::fma(L::add(uz2, mcs), drho, L::fma(L::mul(L::splat(-2.0f), uz), jz, Pzz));
+    const V a110 = L::fma(uxy, drho, L::fma(L::neg(ux), jy, L::fma(L::neg(uy), jx, Pxy)));
+    const V a101 = L::fma(uxz, drho, L::fma(L::neg(ux), jz, L::fma(L::neg(uz), jx, Pxz)));
+    const V a011 = L::fma(uyz, drho, L::fma(L::neg(uy), jz, L::fma(L::neg(uz), jy, Pyz)));
+    // post-collision central moments of d: third and higher orders -w's moments (products of
+    // the 1-D moments (1, -u, u^2) of the D1Q3 weights), second order relaxed
+    const V ex[3] = {L::splat(1.0f), L::neg(ux), ux2}, ey[3] = {L::splat(1.0f), L::neg(uy), uy2},
+            ez[3] = {L::splat(1.0f), L::neg(uz), uz2};
 #pragma unroll
     for (int m = 0; m < Q; ++m) {
-        const int o = order_of(m);
-        const float aw = ex[m % 3] * ey[(m / 3) % 3] * ez[m / 9];
-        if (o >= 3) d[m] = -aw;
+        const int p = m % 3, q = (m / 3) % 3, r = m / 9;
+        if (p + q + r < 3) continue;
+        // a product with unit factors skipped (multiplication by 1 is exact)
+        V aw = ex[p];
+        if (q) aw = p ? L::mul(aw, ey[q]) : ey[q];
+        if (r) aw = (p || q) ? L::mul(aw, ez[r]) : ez[r];
+        d[m] = L::neg(aw);
     }
     d[0] = drho;
-    d[1] = fmaf(0.5f * rho, a.g[0], ux);
-    d[3] = fmaf(0.5f * rho, a.g[1], uy);
-    d[9] = fmaf(0.5f * rho, a.g[2], uz);
-    d[2] = k2 * a200 - s2 * ux2;
-    d[6] = k2 * a020 - s2 * uy2;
-    d[18] = k2 * a002 - s2 * uz2;
-    d[4] = k2 * a110 - s2 * (ux * uy);
-    d[10] = k2 * a101 - s2 * (ux * uz);
-    d[12] = k2 * a011 - s2 * (uy * uz);
-    // inverse T(u)^-1
+    d[1] = L::fma(L::mul(L::splat(0.5f), rho), L::splat(g[0]), ux);
+    d[3] = L::fma(L::mul(L::splat(0.5f), rho), L::splat(g[1]), uy);
+    d[9] = L::fma(L::mul(L::splat(0.5f), rho), L::splat(g[2]), uz);
+    d[2] = L::fma(k2, a200, L::mul(ns2, ux2));
+    d[6] = L::fma(k2, a020, L::mul(ns2, uy2));
+    d[18] = L::fma(k2, a002, L::mul(ns2, uz2));
+    d[4] = L::fma(k2, a110, L::mul(ns2, uxy));
+    d[10] = L::fma(k2, a101, L::mul(ns2, uxz));
+    d[12] = L::fma(k2, a011, L::mul(ns2, uyz));
+    // inverse T(u)^-1: z, then y, then x
+    const V zc = L::add(uz2, L::splat(CS2)), yc = L::add(uy2, L::splat(CS2)), xc = L::add(ux2, L::splat(CS2));
+    const V z2 = L::mul(L::splat(2.0f), uz), y2 = L::mul(L::splat(2.0f), uy), x2 = L::mul(L::splat(2.0f), ux);
 #pragma unroll
     for (int q = 0; q < 3; ++q)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) inv3(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, uz2 + CS2);
+        for (int p = 0; p < 3; ++p) inv3_t<L>(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, zc, z2);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) inv3(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, uy2 + CS2);
+        for (int p = 0; p < 3; ++p) inv3_t<L>(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, yc, y2);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) inv3(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, ux2 + CS2);
+    for (int k = 0; k < 9; ++k) inv3_t<L>(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, xc, x2);
 }
+
+__device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a) { collide_fast_t<Lane1>(d, a.s2, a.g); }
 
 // The classical operators the paper compares against (Sec. 2.1.2), with the second-order
 // equilibrium f_eq2_i = w_i rho [1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u] and the second-order (Guo)
@@ -631,6 +689,66 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     // the active slots are a multiple of 64, so this exit is taken by whole warps
     if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
     step_cell<ST, SCHEME, COLL>(v, src, dst, a, slot, threadIdx.x & 31u);
+}
+
+// Esoteric-twist step with two cells per thread: lane l of a warp updates cells l and l + 32 of
+// one brick (its lz = 0-1 and lz = 2-3 halves), and their collisions run as one stream of packed
+// FP32x2 instructions (the default rates only), which halves the issue slots of the arithmetic;
+// loads, wall rules and stores stay per cell.  A warp covers one brick, so the brick's corner
+// row still goes round by shuffle.  Results are bit-identical to the one-cell kernels.
+template <int ST>
+__device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop, const LevelArgs& a, uint32_t slot,
+                                                 const uint32_t (&cs)[8], uint32_t half, const float (&d)[Q])
+{
+    store_et<ST>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
+    if (half) {
+        const uint32_t rec = (uint32_t)v.aux[slot];
+        const uint32_t nbq = (uint32_t)v.n_bq;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (half & (1u << i)) Store<ST>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
+    }
+}
+
+template <int ST, int BRICKS, int MINB>
+__global__ void __launch_bounds__(BRICKS * 32, MINB)
+    k_step2(DomainView v, void* pop, LevelArgs a)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t brick = blockIdx.x * (uint32_t)BRICKS + (threadIdx.x >> 5);
+    if (brick >= (uint32_t)v.n_bricks) return;  // whole warps
+    const uint32_t n = (uint32_t)v.n_slots;
+    const uint32_t slotA = brick * BRICK_CELLS + lane, slotB = slotA + 32u;
+    const int32_t row = __ldg(v.nb8 + brick * 8u + (lane & 7u));
+    uint32_t csA[8], csB[8];
+    corner_slots_shfl(row, slotA, csA);
+    corner_slots_shfl(row, slotB, csB);
+    const uint32_t wA = __ldg(v.word + slotA), wB = __ldg(v.word + slotB);
+    const bool fA = (wA & WORD_FLUID) != 0u, fB = (wB & WORD_FLUID) != 0u;
+    if (!fA && !fB) return;
+    float dA[Q], dB[Q];
+    if (fA) fetch_et<ST, true>(pop, n, csA, wA & WORD_WALL_MASK, a.parity, dA);
+    if (fB) fetch_et<ST, true>(pop, n, csB, wB & WORD_WALL_MASK, a.parity, dB);
+    const uint32_t halfA =
+        (fA && (wA & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotA, wA, a, dA) : 0u;
+    const uint32_t halfB =
+        (fB && (wB & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotB, wB, a, dB) : 0u;
+    const float s2A = (wA & WORD_OWN_TAU) ? __ldg(v.s2_cell + slotA) : a.s2;
+    const float s2B = (wB & WORD_OWN_TAU) ? __ldg(v.s2_cell + slotB) : a.s2;
+    float2 d2[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d2[i] = make_float2(fA ? dA[i] : 0.0f, fB ? dB[i] : 0.0f);  // a solid lane: rest
+    collide_fast_t<Lane2>(d2, make_float2(s2A, s2B), a.g);
+    if (fA) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dA[i] = d2[i].x;
+        store_twist_cell<ST>(v, pop, a, slotA, csA, halfA, dA);
+    }
+    if (fB) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dB[i] = d2[i].y;
+        store_twist_cell<ST>(v, pop, a, slotB, csB, halfB, dB);
+    }
 }
 
 // Software-pipelined persistent variant of the FP32 esoteric-twist step.  Each CTA walks over
@@ -1005,6 +1123,14 @@ cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const
     });
 }
 
+template <int ST, int BRICKS, int MINB>
+cudaError_t launch_step2(const DomainView& v, void* pop, const LevelArgs& a, cudaStream_t s)
+{
+    if (v.n_bricks == 0) return cudaSuccess;
+    k_step2<ST, BRICKS, MINB><<<grid_for(v.n_bricks, BRICKS), BRICKS * 32, 0, s>>>(v, pop, a);
+    return cudaGetLastError();
+}
+
 template <int BRICKS, int MINB>
 cudaError_t launch_step_et_pipe(const DomainView& v, void* pop, const LevelArgs& a, cudaStream_t s)
 {
@@ -1032,6 +1158,11 @@ cudaError_t launch_step_scheme(int config, const DomainView& v, const void* src,
     if (config == 5) {
         if (ST == LBM_STORE_FP32 && SCHEME == LBM_SCHEME_ESOTERIC) return launch_step_et_pipe<2, 6>(v, dst, a, s);
         config = 3;  // the pipelined variant exists for FP32 twist only
+    }
+    if (config >= 6) {
+        if (SCHEME == LBM_SCHEME_ESOTERIC && a.coll == COLL_CHM_FAST)
+            return config == 6 ? launch_step2<ST, 4, 4>(v, dst, a, s) : launch_step2<ST, 4, 3>(v, dst, a, s);
+        config = 2;  // the two-cell kernels exist for the twist with the default rates only
     }
     switch (config) {
     case 0: return launch_step_t<ST, SCHEME, 4, 3>(v, src, dst, a, s);

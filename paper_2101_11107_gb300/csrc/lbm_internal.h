@@ -85,7 +85,7 @@ struct BatchEntry {
     void* pop;  // the domain's in-place population array
 };
 
-constexpr int N_LAUNCH_CONFIGS = 6;
+constexpr int N_LAUNCH_CONFIGS = 8;
 
 // collision kernels (the `coll` of LevelArgs and the COLL template parameter of the step kernels)
 constexpr int COLL_CHM = 0, COLL_CHM_FAST = 1, COLL_SRT2 = 2, COLL_TRT2 = 3;

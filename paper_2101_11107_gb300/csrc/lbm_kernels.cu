@@ -15,7 +15,8 @@ const Launchers& launchers(int storage)
 
 const char* launch_config_name(int config)
 {
-    static const char* names[N_LAUNCH_CONFIGS] = {"256x3", "128x7", "128x6", "128x8", "128x10", "pipe128x6"};
+    static const char* names[N_LAUNCH_CONFIGS] = {"256x3", "128x7", "128x6", "128x8", "128x10", "pipe128x6",
+                                                            "2c128x4", "2c128x3"};
     return (config >= 0 && config < N_LAUNCH_CONFIGS) ? names[config] : "?";
 }
 

@@ -28,8 +28,8 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_corrector_gradients", "lbm_corrector_train_step", "lbm_corrector_apply", "lbm_corrector_destroy",
            "lbm_apply_velocity_correction", "lbm_restrict", "lbm_mean_reset", "lbm_mean_sample", "lbm_mean_get",
            "lbm_probe", "lbm_similarity_index"]
-N_LAUNCH_CONFIGS = 6
-LAUNCH_CONFIG_NAMES = ["256x3", "128x7", "128x6", "128x8", "128x10", "pipe128x6"]
+N_LAUNCH_CONFIGS = 8
+LAUNCH_CONFIG_NAMES = ["256x3", "128x7", "128x6", "128x8", "128x10", "pipe128x6", "2c128x4", "2c128x3"]
 SCHEME = {"ab": 0, "esoteric": 1}
 COLLISION = {"chm": 0, "srt2": 1, "trt2": 2}
 
