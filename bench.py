@@ -40,11 +40,13 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "womersley_pipe_64x64x256_R28_Wo4_tau0.55"
 METRIC = "fluid MLUPS, D3Q27 CHM-MRT fused stream-collide (% of measured HBM roofline)"
 BYTES_PER_VALUE = {"fp32": 4, "fp16": 2, "bf16": 2}
-# DRAM bytes per launch of the FP32 twist step kernel in launch config 128x6 on this workload,
-# from the ncu capture summarised in profiles/k_step_womersley_fp32_twist.md
-# (79.99 MB read + 18.77 MB write); reported only when the bench runs that configuration
-K_STEP_TRAFFIC_BYTES = 98_760_192
-K_STEP_TRAFFIC_CONFIG = "128x6"
+# DRAM bytes per launch of the FP32 twist step kernel on this workload, per launch
+# configuration, from the ncu captures summarised in profiles/ (dram__bytes_read.sum +
+# dram__bytes_write.sum); reported only for the configuration the bench runs
+K_STEP_TRAFFIC = {
+    "128x6": (98_760_192, "profiles/k_step_womersley_fp32_twist.md"),      # 79.99 + 18.77 MB
+    "2c128x4": (98_807_040, "profiles/k_step2_womersley_fp32_twist.md"),   # 80.02 + 18.78 MB
+}
 
 
 def dist_env():
@@ -393,9 +395,10 @@ def main():
                    "bytes_per_update_algorithmic": 216, "wall_s_timed_loop": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     "traffic": K_STEP_TRAFFIC_BYTES if main["launch_config"] == K_STEP_TRAFFIC_CONFIG else None,
+                     "traffic": K_STEP_TRAFFIC.get(main["launch_config"], (None, None))[0],
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                     "profiles/k_step_womersley_fp32_twist.md)",
+                                     + str(K_STEP_TRAFFIC.get(main["launch_config"], (None, "no capture of this "
+                                                                                        "configuration"))[1]) + ")",
                      "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nbox, "d2h_bytes_per_step": 16 * nbox,
