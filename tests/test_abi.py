@@ -117,3 +117,11 @@ def test_null_arguments(L):
     assert L.lbm_step(None, 1) == 1
     assert L.lbm_sync(None) == 1
     L.lbm_destroy(None)
+
+
+def test_domain_beyond_the_32_bit_offset_range_is_rejected(L):
+    """Kernels address populations with 32-bit offsets i * n_slots + slot: a 544^3 fully
+    periodic box (161 M slots, 27 x slots > 2^32) must be refused before any device work."""
+    mask = np.ones((544, 544, 544), np.uint8)
+    st, msg, h = _create(L, mask, params={"periodic": (1, 1, 1)})
+    assert st == 1 and "too large" in msg and not h.value
