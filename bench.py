@@ -236,6 +236,24 @@ def large_variant(stream, steps=100):
     return out
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The maximum of x over all ranks of the initialised process group (x itself with one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, cells_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job MLUPS of `world` independent replicas that each advanced `cells_per_rank` cells
+    `steps` times, timed by the slowest rank (max_ms for all steps)."""
+    return world * cells_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,12 +356,8 @@ def main():
             main_dom = dom
 
     main = results["fp32"]
-    total_ms = sum(fp32_times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * main["fluid_cells"] * args.steps / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(sum(fp32_times), dev)
+    value = replica_throughput(world, main["fluid_cells"], args.steps, total_ms)
 
     # end to end through the public API, host buffers: upload the initial macroscopic state from
     # pinned host memory, advance 200 steps, read rho and u back to pinned host memory

@@ -1,0 +1,57 @@
+"""The multi-GPU path of the benchmark is replicas (one independent domain per rank, no
+data-path collective); its host logic -- the max-over-ranks timing and the whole-job
+throughput -- checked with two gloo ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 + 5.0 * rank  # rank 1 is the slow one
+        m = bench.max_over_ranks(local_ms)
+        out[rank] = (m, bench.replica_throughput(world, 1000, 20, m))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.start_processes(_rank, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 15.0
+    # 2 replicas x 1000 cells x 20 steps in 15 ms
+    assert abs(res[0][1] - 2 * 1000 * 20 / 15e-3 / 1e6) < 1e-12
+
+
+def test_single_process_passes_through():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.replica_throughput(1, 632832, 100, 3.3) == pytest.approx(632832 * 100 / 3.3e-3 / 1e6)
