@@ -262,6 +262,14 @@ __device__ __forceinline__ void close_open(float (&d)[Q], int kind, int axis, in
 // boundaries.  f*_a(x, n - 1) comes from the cell's own slot (A-B) or from the side buffer
 // (twist: that slot is the one x + c_a pulls and overwrites in this step).  Returns the mask of
 // the q >= 1/2 links, whose f*_a the twist must keep in the side buffer.
+// Position of wall link i of a Bouzidi cell in the packed link lists (q, and the twist side
+// buffer): the cell's entries start at its aux record and follow the set bits of its wall mask
+// in direction order.
+__device__ __forceinline__ uint32_t link_index(uint32_t off, uint32_t wm, int i)
+{
+    return off + (uint32_t)__popc(wm & ((1u << i) - 1u));
+}
+
 template <int ST, int SCHEME>
 __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* src_ab, uint32_t slot,
                                                uint32_t word, const LevelArgs& a, float (&d)[Q])
@@ -270,19 +278,19 @@ __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* 
     const int kind = (int)((word >> WORD_KIND_SHIFT) & 3u);
     uint32_t half = 0u;
     if (kind == KIND_BOUZIDI) {
-        const uint32_t rec = (uint32_t)v.aux[slot];
-        const uint32_t nbq = (uint32_t)v.n_bq;
+        const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if (!(wm & (1u << i))) continue;
-            const float q = __ldg(v.bq + (uint32_t)i * nbq + rec);
+            const uint32_t li = link_index(off, wm, i);
+            const float q = __ldg(v.bq + li);
             if (q > 0.0f) {
                 if (q < 0.5f) {
                     if (!(wm & (1u << (Q - 1 - i)))) d[i] = 2.0f * q * d[i] + (1.0f - 2.0f * q) * d[Q - 1 - i];
                 } else {
                     const float inv2q = 0.5f / q;
                     const float fa = (SCHEME == LBM_SCHEME_ESOTERIC)
-                                         ? Store<ST>::load_rw(v.side, i, (uint32_t)i * nbq + rec)
+                                         ? Store<ST>::load_rw(v.side, i, li)
                                          : Store<ST>::load(src_ab, i, (uint32_t)i * (uint32_t)v.n_slots + slot);
                     d[i] = inv2q * d[i] + (1.0f - inv2q) * fa;
                     half |= 1u << i;
@@ -664,11 +672,10 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         collide_model<COLL>(d, la);
         store_et<ST>(dst, n, cs, a.parity, d);
         if (half) {
-            const uint32_t rec = (uint32_t)v.aux[slot];
-            const uint32_t nbq = (uint32_t)v.n_bq;
+            const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if (half & (1u << i)) Store<ST>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
+                if (half & (1u << i)) Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
         }
     } else {
         const int32_t row = __ldg(v.nbr + brick * (uint32_t)Q + (lane < (uint32_t)Q ? lane : 0u));
@@ -702,11 +709,11 @@ __device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop,
 {
     store_et<ST>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
     if (half) {
-        const uint32_t rec = (uint32_t)v.aux[slot];
-        const uint32_t nbq = (uint32_t)v.n_bq;
+        const uint32_t off = (uint32_t)v.aux[slot];
+        const uint32_t wm = __ldg(v.word + slot) & WORD_WALL_MASK;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            if (half & (1u << i)) Store<ST>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
+            if (half & (1u << i)) Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
     }
 }
 
@@ -818,11 +825,10 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
                 collide_model<COLL>(d, la);
                 store_et<LBM_STORE_FP32>(pop, n, cs, a.parity, d);
                 if (half) {
-                    const uint32_t rec = (uint32_t)v.aux[slot];
-                    const uint32_t nbq = (uint32_t)v.n_bq;
+                    const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (half & (1u << i)) Store<LBM_STORE_FP32>::store(v.side, i, (uint32_t)i * nbq + rec, d[i]);
+                        if (half & (1u << i)) Store<LBM_STORE_FP32>::store(v.side, i, link_index(off, wm, i), d[i]);
                 }
             }
         }
@@ -958,9 +964,11 @@ __global__ void __launch_bounds__(256)
         store_et<ST>(dst, n, cs, parity_prev, d);
         const uint32_t word = v.word[slot];
         if (((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) {
-            const uint32_t rec = (uint32_t)v.aux[slot];
+            const uint32_t off = (uint32_t)v.aux[slot];
+            const uint32_t wm = word & WORD_WALL_MASK;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) Store<ST>::store(v.side, i, (uint32_t)i * (uint32_t)v.n_bq + rec, d[i]);
+            for (int i = 0; i < Q; ++i)
+                if ((wm >> i) & 1u) Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
         }
     } else {
 #pragma unroll
@@ -1017,13 +1025,14 @@ __global__ void __launch_bounds__(256)
         }
         const uint32_t word = v.word[slot];
         if (((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) {
-            const uint32_t rec = (uint32_t)v.aux[slot];
-            const uint32_t nbq = (uint32_t)v.n_bq;
+            const uint32_t off0 = (uint32_t)v.aux[slot];
+            const uint32_t wm = word & WORD_WALL_MASK;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const uint32_t off = (uint32_t)i * nbq + rec;
-                Store<ST>::store(v.side, i, off, Store<ST>::load_rw(v.side, i, off) + delta[i]);
-            }
+            for (int i = 0; i < Q; ++i)
+                if ((wm >> i) & 1u) {
+                    const uint32_t off = link_index(off0, wm, i);
+                    Store<ST>::store(v.side, i, off, Store<ST>::load_rw(v.side, i, off) + delta[i]);
+                }
         }
     } else {
 #pragma unroll

@@ -35,6 +35,7 @@ struct lbm_domain {
     int32_t nx = 0, ny = 0, nz = 0;
     lbm_params params{};
     int64_t n_fluid = 0, n_bricks = 0, n_store_bricks = 0, n_slots = 0, n_bq = 0, n_io = 0, n_wall = 0;
+    int64_t n_blinks = 0;  // wall links of the Bouzidi cells (length of the packed link lists)
     DomainView view{};
     int32_t* d_fl_slot = nullptr;
     int32_t* d_fl_box = nullptr;
@@ -42,7 +43,7 @@ struct lbm_domain {
     // A-B: d_pop[cur] holds the post-collision populations of level time - 1; esoteric twist:
     // d_pop[0] holds them in place, arranged for a read of parity time & 1
     int cur = 0;
-    void* d_side = nullptr;  // twist: f* of q >= 1/2 Bouzidi links, [27][n_bq]
+    void* d_side = nullptr;  // twist: f* of q >= 1/2 Bouzidi links, one entry per packed link
     int launch_config = DEFAULT_LAUNCH_CONFIG;
     double* d_partials = nullptr;
     lbm_diagnostics* d_diag = nullptr;
@@ -65,7 +66,7 @@ struct lbm_domain {
 
     int bytes_per_value() const { return params.storage == LBM_STORE_FP32 ? 4 : 2; }
     size_t pop_bytes() const { return (size_t)Q * (size_t)n_slots * (size_t)bytes_per_value(); }
-    size_t side_bytes() const { return (size_t)Q * (size_t)std::max<int64_t>(n_bq, 1) * (size_t)bytes_per_value(); }
+    size_t side_bytes() const { return (size_t)std::max<int64_t>(n_blinks, 1) * (size_t)bytes_per_value(); }
     bool twist() const { return params.scheme == LBM_SCHEME_ESOTERIC; }
     void* src() const { return d_pop[twist() ? 0 : cur]; }
     void* dst() const { return d_pop[twist() ? 0 : 1 - cur]; }
@@ -407,18 +408,29 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
             return fail(LBM_ERR_INVALID_ARG, "duplicate link");
         if (l == 0 || lk[l].first != lk[l - 1].first) ++n_bq;
     }
-    std::vector<float> bq((size_t)Q * (size_t)std::max<int64_t>(n_bq, 1), 0.0f);
-    {
-        int64_t rec = -1;
-        for (size_t l = 0; l < lk.size(); ++l) {
-            if (l == 0 || lk[l].first != lk[l - 1].first) {
-                ++rec;
-                word[(size_t)lk[l].first] |= (uint32_t)KIND_BOUZIDI << WORD_KIND_SHIFT;
-                aux[(size_t)lk[l].first] = (int32_t)rec;
-            }
-            bq[(size_t)lk[l].second.first * (size_t)n_bq + (size_t)rec] = lk[l].second.second;
+    // Packed link lists: each Bouzidi cell (in slot order) owns the entries [aux, aux + number of
+    // its wall links) of the q list and of the twist side buffer, one per wall link in direction
+    // order (q = 0 for a wall link without q: halfway bounce-back), so that the few links of a
+    // cell share one or two sectors.
+    std::vector<float> bq;
+    for (size_t l = 0; l < lk.size();) {
+        const int64_t s = lk[l].first;
+        const uint32_t wmk = word[(size_t)s] & WORD_WALL_MASK;
+        float qq[Q] = {};
+        size_t e = l;
+        for (; e < lk.size() && lk[e].first == s; ++e) {
+            if (!((wmk >> lk[e].second.first) & 1u))
+                return fail(LBM_ERR_INVALID_ARG, "a Bouzidi link does not cross a wall link of its cell");
+            qq[lk[e].second.first] = lk[e].second.second;
         }
+        if (bq.size() + Q >= ((size_t)1 << 31)) return fail(LBM_ERR_INVALID_ARG, "too many Bouzidi links");
+        word[(size_t)s] |= (uint32_t)KIND_BOUZIDI << WORD_KIND_SHIFT;
+        aux[(size_t)s] = (int32_t)bq.size();
+        for (int i = 0; i < Q; ++i)
+            if ((wmk >> i) & 1u) bq.push_back(qq[i]);
+        l = e;
     }
+    const int64_t n_blinks = (int64_t)bq.size();
 
     // ---------------------------------------------------------------- device
     lbm_domain* D = new (std::nothrow) lbm_domain();
@@ -432,6 +444,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     D->n_store_bricks = n_store;
     D->n_slots = n_slots;
     D->n_bq = n_bq;
+    D->n_blinks = n_blinks;
     D->n_io = (int64_t)io_phi.size();
     D->n_wall = n_wall;
     D->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -506,7 +519,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     v.s2_cell = d_s2;
     v.aux = d_aux;
     v.bq = d_bq;
-    v.n_bq = std::max<int64_t>(n_bq, 1);
+    v.n_bq = std::max<int64_t>(n_blinks, 1);
     v.io_phi = d_io_phi;
     v.io_axis = d_io_axis;
     v.io_sign = d_io_sign;
@@ -909,7 +922,7 @@ lbm_status lbm_save_state(lbm_domain* D, const char* path)
     if (e != cudaSuccess) return cuda_fail(e, "reading populations");
     CheckpointHeader H{};
     std::memcpy(H.magic, kMagic, 8);
-    H.version = 2;
+    H.version = 3;
     H.nx = D->nx;
     H.ny = D->ny;
     H.nz = D->nz;
@@ -943,7 +956,7 @@ lbm_status lbm_load_state(lbm_domain* D, const char* path)
     if (!f) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
     CheckpointHeader H{};
     bool ok = std::fread(&H, sizeof(H), 1, f) == 1;
-    if (!ok || std::memcmp(H.magic, kMagic, 8) != 0 || H.version != 2) {
+    if (!ok || std::memcmp(H.magic, kMagic, 8) != 0 || H.version != 3) {
         std::fclose(f);
         return fail(LBM_ERR_IO, "not a checkpoint of this library");
     }

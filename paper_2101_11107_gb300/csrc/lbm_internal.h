@@ -51,9 +51,11 @@ struct DomainView {
     const uint32_t* word;   // [64 n_bricks]
     const int32_t* aux;     // [64 n_bricks] record of a Bouzidi or open-boundary cell
     const float* s2_cell;   // [64 n_bricks] second-order rate of cells with WORD_OWN_TAU
-    const float* bq;        // [27][n_bq] Bouzidi q of the link whose unknown is i (0: halfway BB)
-    void* side;             // twist: [27][n_bq] f*_i of the previous step at Bouzidi cells (storage type)
-    int64_t n_bq;
+    const float* bq;        // [n_bq] q of every wall link of the Bouzidi cells, packed per cell: cell
+                            // (aux record a, wall mask wm) owns a .. a + popc(wm) - 1 in direction
+                            // order (0: halfway bounce-back on that link)
+    void* side;             // twist: [n_bq] f*_i of the previous step, same packing (storage type)
+    int64_t n_bq;           // packed links (at least 1)
     const float* io_phi;    // [n_io] inflow profile factor 2 (1 - r^2/R^2)
     const int8_t* io_axis;  // [n_io] inward normal axis
     const int8_t* io_sign;  // [n_io] inward normal sign
