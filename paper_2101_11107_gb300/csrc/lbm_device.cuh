@@ -284,14 +284,15 @@ __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* 
             if (!(wm & (1u << i))) continue;
             const uint32_t li = link_index(off, wm, i);
             const float q = __ldg(v.bq + li);
+            // loaded whatever q is, so that the two loads do not wait on each other
+            const float fa = (SCHEME == LBM_SCHEME_ESOTERIC)
+                                 ? Store<ST>::load_rw(v.side, i, li)
+                                 : Store<ST>::load(src_ab, i, (uint32_t)i * (uint32_t)v.n_slots + slot);
             if (q > 0.0f) {
                 if (q < 0.5f) {
                     if (!(wm & (1u << (Q - 1 - i)))) d[i] = 2.0f * q * d[i] + (1.0f - 2.0f * q) * d[Q - 1 - i];
                 } else {
                     const float inv2q = 0.5f / q;
-                    const float fa = (SCHEME == LBM_SCHEME_ESOTERIC)
-                                         ? Store<ST>::load_rw(v.side, i, li)
-                                         : Store<ST>::load(src_ab, i, (uint32_t)i * (uint32_t)v.n_slots + slot);
                     d[i] = inv2q * d[i] + (1.0f - inv2q) * fa;
                     half |= 1u << i;
                 }
