@@ -393,6 +393,10 @@ def main():
     if rank == 0 and world == 1:
         v, thr, desc = run_oracle_sample(args.cpu_seconds)
         cpu = {"value": v, "unit": "MLUPS", "cores": thr, "kind": "oracle", "sample": desc}
+        # the same oracle on one core, a shorter sample
+        v1, _, desc1 = run_oracle_sample(max(1.0, args.cpu_seconds / 3), threads=1)
+        run_oracle_sample(0.0, threads=thr)  # back to all cores
+        cpu["single_core"] = {"value": v1, "unit": "MLUPS", "cores": 1, "sample": desc1}
 
     if rank != 0:
         return
