@@ -229,7 +229,8 @@ lbm_status lbm_set_launch_config(lbm_domain* dom, int32_t config);
 
 /* Times every launch configuration on this domain (trial_steps steps each, CUDA events on the
  * domain's stream) and selects the fastest.  The domain's populations and time level are left
- * as they were.  ms_per_step (may be NULL) receives LBM_N_LAUNCH_CONFIGS times; *best_config
+ * as they were.  ms_per_step (may be NULL) receives LBM_N_LAUNCH_CONFIGS times (-1 for a
+ * configuration that has no kernel of its own for this domain and is not timed); *best_config
  * (may be NULL) the choice.  Waits for the stream.  Allocates one population array while it
  * runs.  Errors: INVALID_ARG, OOM, CUDA. */
 lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_config, float* ms_per_step);
@@ -248,9 +249,10 @@ lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_conf
  *     CUDA.
  *   lbm_batch_step: n >= 0 steps of every domain (each domain's time advances by n); waits for
  *     the previous chunk before refilling its host argument table.
- *   lbm_batch_set_launch_config / lbm_batch_autotune: as for single domains; autotune keeps every
- *     domain's state (it copies and restores the populations) and needs trial_steps <=
- *     graph_steps.
+ *   lbm_batch_set_launch_config / lbm_batch_autotune: as for single domains (the batched kernel
+ *     has configurations 0-4; the others run as 4, and autotune does not time them); autotune
+ *     keeps every domain's state (it copies and restores the populations) and needs trial_steps
+ *     <= graph_steps.
  */
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_steps, void* cuda_stream,

@@ -620,6 +620,16 @@ lbm_status lbm_set_launch_config(lbm_domain* D, int32_t config)
     return LBM_OK;
 }
 
+// Whether a launch configuration has its own kernel for this domain (otherwise the launcher
+// falls back to another configuration, which the autotuner then need not time again).
+static bool config_applies(const lbm_domain* D, int c)
+{
+    const bool twist = D->params.scheme == LBM_SCHEME_ESOTERIC;
+    if (c == 5) return twist && D->params.storage == LBM_STORE_FP32;
+    if (c == 6 || c == 7) return twist && D->level_args(0).coll == COLL_CHM_FAST;
+    return true;
+}
+
 lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config, float* ms_per_step)
 {
     g_last_error.clear();
@@ -642,6 +652,10 @@ lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config
     int best = D->launch_config;
     float best_ms = INFINITY;
     for (int c = 0; c < N_LAUNCH_CONFIGS && e == cudaSuccess; ++c) {
+        if (!config_applies(D, c)) {
+            if (ms_per_step) ms_per_step[c] = -1.0f;
+            continue;
+        }
         // one untimed step, then trial_steps timed steps, with the level arguments of the
         // domain's next levels (parity alternates as in a real run)
         int cur = D->cur;
@@ -1231,6 +1245,10 @@ lbm_status lbm_batch_autotune(lbm_batch* B, int32_t trial_steps, int32_t* best_c
     if (!st && e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
     if (!st && e == cudaSuccess) B->fill_args(trial_steps);
     for (int c = 0; c < N_LAUNCH_CONFIGS && !st && e == cudaSuccess; ++c) {
+        if (c >= 5) {  // the batched kernel has the one-cell configurations 0-4 only
+            if (ms_per_step) ms_per_step[c] = -1.0f;
+            continue;
+        }
         e = B->enqueue_steps(1, c);  // untimed
         if (e == cudaSuccess) e = cudaEventRecord(t0, B->stream);
         if (e == cudaSuccess) e = B->enqueue_steps(trial_steps, c);

@@ -156,3 +156,18 @@ def test_srt_fails_where_chm_mrt_runs():
         assert case["chm"]["failed_at_step"] is None, case
         assert case["srt2"]["failed_at_step"] is not None, case
         assert case["chm"]["max_u"] < 0.2
+
+
+def test_autotune_times_only_configurations_with_their_own_kernel():
+    """The two-cell kernels exist for CHM-MRT at unit higher-order rates and the pipelined one
+    for FP32 storage; elsewhere those configurations fall back and are reported as -1."""
+    g = I.aneurysm(1, edge=64, period=400.0, reynolds=20.0)
+    d = lbm.Domain.from_geometry(g, collision="srt2")
+    best, ms = d.autotune(3)
+    assert ms["2c128x4"] == -1 and ms["2c128x3"] == -1 and ms["pipe128x6"] > 0
+    assert best not in (lbm.LAUNCH_CONFIG_NAMES.index("2c128x4"), lbm.LAUNCH_CONFIG_NAMES.index("2c128x3"))
+    d.close()
+    d = lbm.Domain.from_geometry(g, storage="fp16")
+    best, ms = d.autotune(3)
+    assert ms["pipe128x6"] == -1 and ms["2c128x4"] > 0
+    d.close()
