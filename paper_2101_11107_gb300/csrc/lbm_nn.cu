@@ -64,10 +64,13 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 
 // ------------------------------------------------------------------------------ tcgen05 conv
 // out[p][co] = act(sum_o sum_ci w[o][co][ci] in[p + o][ci] + bias[co]), zeroed where gate <= 0,
-// as an implicit GEMM on the 5th-generation tensor cores.  A CTA of 128 threads computes one
-// slab of 8 (x) x 16 (y) x 1 (z) cells: M = 128 rows (cell x + 8 y), N = 16 output channels,
-// K = 27 offsets x 16 input channels, i.e. 27 tcgen05.mma (kind::f16, BF16 in, FP32 accumulator
-// of 128 lanes x 16 columns in tensor memory) issued by one thread.
+// as an implicit GEMM on the 5th-generation tensor cores.  A slab is 8 (x) x 16 (y) x 1 (z)
+// cells: M = 128 rows (cell x + 8 y), N = 16 output channels, K = 27 offsets x 16 input
+// channels, i.e. 27 tcgen05.mma (kind::f16, BF16 in, FP32 accumulator of 128 lanes x 16 columns
+// in tensor memory) issued by one thread.  The CTAs (128 threads) are persistent and walk over
+// slabs blockIdx.x, + gridDim.x, ...: the weights are staged once per CTA, the halo of the next
+// slab is loaded into the other of two buffers, and two accumulators alternate, so the 27 MMAs
+// of slab j run while the epilogue of slab j - 1 drains and the halo of slab j + 1 arrives.
 //   * The slab's halo (10 x 18 x 3 cells) comes in by two TMA tile loads of the channels-last
 //     padded activations (a 4-D tensor map, box 8 channels x 10 x 18 x 3), one per group of 8
 //     channels, so shared memory holds two "planes" of 16 bytes per cell.  For offset o the A
@@ -75,8 +78,8 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
 //     8-row core matrices are 8 consecutive cells along x (16 B apart), core matrices along M
 //     are the 16 y rows (160 B apart), and the two K core matrices are the two planes.  No
 //     gather, no copy: the 27 descriptors differ only in their start address.
-//   * B (the 27 weight blocks, N x K = 16 x 16) is staged once per CTA in the same canonical
-//     layout (core matrix (n-group, k-group) at 128-byte steps).
+//   * B (the 27 weight blocks, N x K = 16 x 16) is staged in the same canonical layout (core
+//     matrix (n-group, k-group) at 128-byte steps).
 //   * The epilogue reads each row back with tcgen05.ld (warp w owns lanes 32w..32w+31), adds the
 //     bias, applies ReLU and the gate, and writes 32 bytes per cell.
 // Every wait (TMA, MMA completion) is bounded; on a timeout the CTA flags the error, waits for
@@ -85,8 +88,10 @@ constexpr int SL_X = 8, SL_Y = 16;                      // slab = M = 128 cells
 constexpr int HX = SL_X + 2, HY = SL_Y + 2, HZ = 3;     // halo
 constexpr uint32_t PLANE_BYTES = HX * HY * HZ * 16;     // 8640: one TMA box
 constexpr uint32_t PLANE_STRIDE = 8704;                 // 128-byte aligned plane step
-constexpr uint32_t W_OFF = 2 * PLANE_STRIDE;            // weights after the two planes
-constexpr uint32_t CONV_SMEM = W_OFF + 27 * 512;        // 31232 B
+constexpr uint32_t HALO_BYTES = 2 * PLANE_STRIDE;       // one halo buffer: two planes
+constexpr uint32_t W_OFF = 2 * HALO_BYTES;              // weights after the two halo buffers
+constexpr uint32_t CONV_SMEM = W_OFF + 27 * 512;        // 48640 B
+constexpr int CONV_CTAS_PER_SM = 4;
 constexpr int TC_WAIT_LIMIT = 1 << 22;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -119,35 +124,47 @@ template <bool OUT_F32>
 __global__ void __launch_bounds__(128)
     k_conv_tc(const __grid_constant__ CUtensorMap tin, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
               int relu, const __nv_bfloat16* __restrict__ gate, void* __restrict__ out, const int4* __restrict__ slabs,
-              Box b, unsigned int* __restrict__ err)
+              int n_slabs, Box b, unsigned int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ __align__(8) uint64_t bar_tma[2], bar_mma[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 sl = slabs[blockIdx.x];
+    const int G = gridDim.x;
+    const int J = (n_slabs - (int)blockIdx.x + G - 1) / G;  // slabs of this CTA (>= 1)
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_tma)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_mma)) : "memory");
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_tma[k])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_mma[k])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(su32(&tmem_base))
+    if (warp == 0) {  // two accumulators of 16 columns, at columns 0 and 32
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(su32(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0) {  // halo: padded coordinates (x0, y0, z) .. + (9, 17, 2), channels 0-7 and 8-15
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&bar_tma)),
-                     "r"(2u * PLANE_BYTES)
+    // halo of slab j into buffer j & 1: padded coordinates (x0, y0, z) .. + (9, 17, 2), channels
+    // 0-7 and 8-15 (issued by thread 0)
+    auto load_halo = [&](int j) {
+        const int4 sl = slabs[blockIdx.x + j * G];
+        uint64_t* bar = &bar_tma[j & 1];
+        unsigned char* dst = smem + (j & 1) * HALO_BYTES;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(2u * PLANE_BYTES)
                      : "memory");
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int c = 0; c < 2; ++c)
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                "%4, %5}], [%6];" ::"r"(su32(smem + j * PLANE_STRIDE)),
-                "l"(reinterpret_cast<uint64_t>(&tin)), "r"(8 * j), "r"(sl.x), "r"(sl.y), "r"(sl.z), "r"(su32(&bar_tma))
+                "%4, %5}], [%6];" ::"r"(su32(dst + c * PLANE_STRIDE)),
+                "l"(reinterpret_cast<uint64_t>(&tin)), "r"(8 * c), "r"(sl.x), "r"(sl.y), "r"(sl.z), "r"(su32(bar))
                 : "memory");
+    };
+    if (tid == 0) {
+        load_halo(0);
+        if (J > 1) load_halo(1);
     }
     // weights: chunk (o, co, j) = w[o][co][8j..8j+7] -> core matrix (co / 8, j) of block o
     for (int q = tid; q < 27 * 16 * 2; q += 128) {
@@ -156,35 +173,21 @@ __global__ void __launch_bounds__(128)
             __ldg(reinterpret_cast<const uint4*>(w) + q);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights visible to the tensor cores
-    const bool halo_ok = __syncthreads_and(tc_wait(&bar_tma, 0)) != 0;  // one decision for the CTA
+    __syncthreads();
     const uint32_t tbase = tmem_base;
-    if (halo_ok && tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = su32(smem), w0 = su32(smem + W_OFF);
-#pragma unroll 1
-        for (int o = 0; o < 27; ++o) {
-            const uint32_t ox = o % 3, oy = (o / 3) % 3, oz = o / 9;
-            const uint64_t ad = smem_desc(a0 + 16u * ((oz * HY + oy) * HX + ox), PLANE_STRIDE, HX * 16);
-            const uint64_t bd = smem_desc(w0 + 512u * (uint32_t)o, 128, 256);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tbase),
-                "l"(ad), "l"(bd), "r"(CONV_IDESC), "r"((uint32_t)(o > 0))
-                : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         su32(&bar_mma))
-                     : "memory");
-    }
-    const bool mma_ok = halo_ok && __syncthreads_and(tc_wait(&bar_mma, 0)) != 0;
-    if (mma_ok) {
+    float bz[CH];
+#pragma unroll
+    for (int co = 0; co < CH; ++co) bz[co] = bias ? __ldg(bias + co) : 0.0f;
+    // epilogue of slab j: accumulator j & 1 -> bias, ReLU, gate -> output
+    auto epilogue = [&](int j) {
+        const int4 sl = slabs[blockIdx.x + j * G];
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t r[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(tbase + ((uint32_t)(warp * 32) << 16)));
+            : "r"(tbase + 32u * (uint32_t)(j & 1) + ((uint32_t)(warp * 32) << 16)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int m = warp * 32 + lane;
         const int x = sl.x + (m & 7), y = sl.y + (m >> 3), z = sl.z;
@@ -193,8 +196,7 @@ __global__ void __launch_bounds__(128)
             const size_t pc = pidx(b, x, y, z);
 #pragma unroll
             for (int co = 0; co < CH; ++co) {
-                float t = __uint_as_float(r[co]);
-                if (bias) t += __ldg(bias + co);
+                float t = __uint_as_float(r[co]) + bz[co];
                 if (relu) t = fmaxf(t, 0.0f);
                 if (gate && !(__bfloat162float(gate[pc * CH + co]) > 0.0f)) t = 0.0f;
                 v[co] = t;
@@ -214,15 +216,65 @@ __global__ void __launch_bounds__(128)
                 dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
-    } else {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+    // give up: flag the error, wait (bounded) for the halo loads t0..t1 and the MMA groups
+    // m0..m1 still in flight
+    auto abandon = [&](int t0, int t1, int m0, int m1) {
         if (tid == 0) atomicOr(err, 1u);
-        // wait (bounded) for what is still in flight before the tensor memory is freed
-        if (!halo_ok) tc_wait(&bar_tma, 0);
-        else tc_wait(&bar_mma, 0);
+        for (int j = t0; j <= t1 && j < J; ++j) tc_wait(&bar_tma[j & 1], (j >> 1) & 1);
+        for (int j = m0 < 0 ? 0 : m0; j <= m1; ++j) tc_wait(&bar_mma[j & 1], (j >> 1) & 1);
+    };
+    bool ok = true;
+    for (int j = 0; j < J; ++j) {
+        // in flight here: halo loads j (and 1 when j = 0), MMA group j - 1
+        if (!__syncthreads_and(tc_wait(&bar_tma[j & 1], (j >> 1) & 1))) {  // one decision for the CTA
+            abandon(j, j == 0 ? 1 : j, j - 1, j - 1);
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = su32(smem + (j & 1) * HALO_BYTES), w0 = su32(smem + W_OFF);
+            const uint32_t d = tbase + 32u * (uint32_t)(j & 1);
+#pragma unroll 1
+            for (int o = 0; o < 27; ++o) {
+                const uint32_t ox = o % 3, oy = (o / 3) % 3, oz = o / 9;
+                const uint64_t ad = smem_desc(a0 + 16u * ((oz * HY + oy) * HX + ox), PLANE_STRIDE, HX * 16);
+                const uint64_t bd = smem_desc(w0 + 512u * (uint32_t)o, 128, 256);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                    "p;\n}\n" ::"r"(d),
+                    "l"(ad), "l"(bd), "r"(CONV_IDESC), "r"((uint32_t)(o > 0))
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&bar_mma[j & 1]))
+                         : "memory");
+        }
+        if (j >= 1) {
+            const int p = j - 1;
+            // in flight here: MMA groups j - 1 and j, no halo load
+            if (!__syncthreads_and(tc_wait(&bar_mma[p & 1], (p >> 1) & 1))) {
+                abandon(J, J - 1, p, j);
+                ok = false;
+                break;
+            }
+            epilogue(p);
+            __syncthreads();  // accumulator p & 1 read; halo buffer p & 1 consumed by MMA p
+            if (tid == 0 && j + 1 < J) load_halo(j + 1);
+        }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (ok) {
+        const int p = J - 1;
+        if (__syncthreads_and(tc_wait(&bar_mma[p & 1], (p >> 1) & 1))) {
+            epilogue(p);
+        } else if (tid == 0) {
+            atomicOr(err, 1u);
+        }
+    }
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tbase) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase) : "memory");
 }
 
 // dW[o][co][ci] += sum_p dy[p][co] x[p + o][ci] and db[co] += sum_p dy[p][co] over the tiles;
@@ -537,10 +589,14 @@ struct lbm_corrector {
         int t = 0;
         while (t < 5 && tmap_of[t] != in) ++t;
         if (t == 5) return cudaErrorInvalidValue;
-        if (f32)
-            k_conv_tc<true><<<(int)n_slabs, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, box, err);
-        else
-            k_conv_tc<false><<<(int)n_slabs, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, box, err);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = (int)std::min<int64_t>(n_slabs, (int64_t)sms * CONV_CTAS_PER_SM);
+        auto k = f32 ? k_conv_tc<true> : k_conv_tc<false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CONV_SMEM);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, (int)n_slabs, box, err);
         return cudaGetLastError();
     }
     // nonzero device error word (read after the stream has been synchronised)
