@@ -359,14 +359,29 @@ __global__ void __launch_bounds__(128)
     if (threadIdx.x < CH) atomicAdd(&db[threadIdx.x], dbacc);
 }
 
-// Input features on the padded box: u / u_scale (3), (rho - 1) / rho_scale, fluid mask, zeros.
-__global__ void k_features(const float* __restrict__ rho, const float* __restrict__ u, const uint8_t* __restrict__ mask,
-                           Box b, float inv_us, float inv_rs, __nv_bfloat16* __restrict__ x0)
+// The elementwise kernels of the corrector run over the slabs of the convolutions (one CTA of
+// 128 threads per 8 x 16 x 1 slab), which cover every cell a call's masks can select (they lie
+// inside the creation mask) -- a tenth of the coarse box or less; the other cells of the padded
+// activations and of the output gradient stay zero from creation.
+__device__ __forceinline__ bool slab_cell(const int4* slabs, const Box& b, int& x, int& y, int& z, int64_t& c)
 {
+    const int4 sl = slabs[blockIdx.x];
+    x = sl.x + (int)(threadIdx.x & 7u);
+    y = sl.y + (int)(threadIdx.x >> 3);
+    z = sl.z;
+    c = ((int64_t)z * b.ny + y) * b.nx + x;
+    return x < b.nx && y < b.ny;
+}
+
+// Input features on the padded box: u / u_scale (3), (rho - 1) / rho_scale, fluid mask, zeros.
+__global__ void __launch_bounds__(128) k_features(const float* __restrict__ rho, const float* __restrict__ u,
+                                                  const uint8_t* __restrict__ mask, Box b, float inv_us, float inv_rs,
+                                                  __nv_bfloat16* __restrict__ x0, const int4* __restrict__ slabs)
+{
+    int x, y, z;
+    int64_t c;
+    if (!slab_cell(slabs, b, x, y, z, c)) return;
     const int64_t n = (int64_t)b.nx * b.ny * b.nz;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    const int x = (int)(c % b.nx), y = (int)((c / b.nx) % b.ny), z = (int)(c / ((int64_t)b.nx * b.ny));
     const float fl = mask[c] ? 1.0f : 0.0f;
     __nv_bfloat16 v[CH];
     v[0] = __float2bfloat16_rn(u[c] * inv_us * fl);
@@ -381,12 +396,16 @@ __global__ void k_features(const float* __restrict__ rho, const float* __restric
     dst[1] = *reinterpret_cast<uint4*>(&v[8]);
 }
 
-// du = du_scale * clamp(O[0:3], -clip, clip) at fluid cells, 0 elsewhere (three planes).
-__global__ void k_output(const float* __restrict__ o4, const uint8_t* __restrict__ mask, int64_t n, float du_scale,
-                         float clip, float* __restrict__ du)
+// du = du_scale * clamp(O[0:3], -clip, clip) at the masked cells of the slabs, 0 at their other
+// cells (three planes; the caller zeroes the rest of the box).
+__global__ void __launch_bounds__(128) k_output(const float* __restrict__ o4, const uint8_t* __restrict__ mask, Box b,
+                                                float du_scale, float clip, float* __restrict__ du,
+                                                const int4* __restrict__ slabs)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    int x, y, z;
+    int64_t c;
+    if (!slab_cell(slabs, b, x, y, z, c)) return;
+    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
     const float fl = mask[c] ? du_scale : 0.0f;
     du[c] = fminf(fmaxf(o4[c * 4 + 0], -clip), clip) * fl;
     du[n + c] = fminf(fmaxf(o4[c * 4 + 1], -clip), clip) * fl;
@@ -395,50 +414,47 @@ __global__ void k_output(const float* __restrict__ o4, const uint8_t* __restrict
 
 // Loss = mean over fluid cells and components of (O - T)^2, T = (u_target - u) / du_scale;
 // dO = 2 (O - T) / N at fluid cells (BF16, padded, channels 0..2).
-__global__ void k_count(const uint8_t* __restrict__ mask, int64_t n, unsigned long long* __restrict__ count)
+__global__ void __launch_bounds__(128) k_count(const uint8_t* __restrict__ mask, Box b, const int4* __restrict__ slabs,
+                                               unsigned long long* __restrict__ count)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned int ballot = __ballot_sync(0xffffffffu, c < n && mask[c] != 0);
+    int x, y, z;
+    int64_t c;
+    const bool in = slab_cell(slabs, b, x, y, z, c);
+    const unsigned int ballot = __ballot_sync(0xffffffffu, in && mask[c] != 0);
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(count, (unsigned long long)__popc(ballot));
 }
 
-__global__ void k_loss(const float* __restrict__ o4, const float* __restrict__ u, const float* __restrict__ ut,
-                       const uint8_t* __restrict__ mask, Box b, float inv_du, const unsigned long long* __restrict__ count,
-                       __nv_bfloat16* __restrict__ dO, double* __restrict__ loss)
+__global__ void __launch_bounds__(128) k_loss(const float* __restrict__ o4, const float* __restrict__ u,
+                                              const float* __restrict__ ut, const uint8_t* __restrict__ mask, Box b,
+                                              float inv_du, const unsigned long long* __restrict__ count,
+                                              __nv_bfloat16* __restrict__ dO, double* __restrict__ loss,
+                                              const int4* __restrict__ slabs)
 {
-    __shared__ double sh[8];
+    __shared__ double sh[4];
     const float two_over_n = *count ? 2.0f / (3.0f * (float)*count) : 0.0f;
     const int64_t n = (int64_t)b.nx * b.ny * b.nz;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int x, y, z;
+    int64_t c;
     double part = 0.0;
-    if (c < n) {
-        // zero the output gradient of every cell, so that a mask differing from the previous
-        // call's leaves no stale values behind
-        const int x = (int)(c % b.nx), y = (int)((c / b.nx) % b.ny), z = (int)(c / ((int64_t)b.nx * b.ny));
+    if (slab_cell(slabs, b, x, y, z, c)) {
+        // every slab cell is written (zero off the mask), so that a mask differing from the
+        // previous call's leaves no stale gradient behind
         __nv_bfloat16* d = dO + pidx(b, x, y, z) * CH;
-        const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-        d[0] = zero;
-        d[1] = zero;
-        d[2] = zero;
-    }
-    if (c < n && mask[c]) {
-        const int x = (int)(c % b.nx), y = (int)((c / b.nx) % b.ny), z = (int)(c / ((int64_t)b.nx * b.ny));
-        __nv_bfloat16* d = dO + pidx(b, x, y, z) * CH;
+        const bool on = mask[c] != 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float r = o4[c * 4 + k] - (ut[k * n + c] - u[k * n + c]) * inv_du;
-            part += (double)r * r;
+            float r = 0.0f;
+            if (on) {
+                r = o4[c * 4 + k] - (ut[k * n + c] - u[k * n + c]) * inv_du;
+                part += (double)r * r;
+            }
             d[k] = __float2bfloat16_rn(two_over_n * r);
         }
     }
     for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        atomicAdd(loss, s);
-    }
+    if (threadIdx.x == 0) atomicAdd(loss, (sh[0] + sh[1]) + (sh[2] + sh[3]));
 }
 
 // BF16 forward weights and, for layers 2 and 3, the data-gradient kernels
@@ -609,8 +625,9 @@ struct lbm_corrector {
     }
     cudaError_t forward(const uint8_t* cmask, const float* r, const float* uu)
     {
-        k_features<<<blocks(n_cells, 256), 256, 0, stream>>>(r, uu, cmask ? cmask : mask, box, 1.0f / u_scale,
-                                                             1.0f / rho_scale, x0);
+        if (n_slabs == 0) return cudaSuccess;
+        k_features<<<(unsigned)n_slabs, 128, 0, stream>>>(r, uu, cmask ? cmask : mask, box, 1.0f / u_scale,
+                                                          1.0f / rho_scale, x0, slabs);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = conv(x0, wb, bmaster(0), 1, nullptr, y1, false);
         if (e == cudaSuccess) e = conv(y1, wb + NW, bmaster(1), 1, nullptr, y2, false);
@@ -624,8 +641,10 @@ struct lbm_corrector {
         if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
-        k_count<<<blocks(n_cells, 256), 256, 0, stream>>>(mk, n_cells, count);
-        k_loss<<<blocks(n_cells, 256), 256, 0, stream>>>(o4, uu, ut, mk, box, 1.0f / du_scale, count, dO, loss);
+        if (n_slabs) {
+            k_count<<<(unsigned)n_slabs, 128, 0, stream>>>(mk, box, slabs, count);
+            k_loss<<<(unsigned)n_slabs, 128, 0, stream>>>(o4, uu, ut, mk, box, 1.0f / du_scale, count, dO, loss, slabs);
+        }
         e = cudaGetLastError();
         const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_tiles, 1), 304);
         if (e == cudaSuccess && n_tiles)
@@ -766,6 +785,7 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
     for (__nv_bfloat16* p : {K->x0, K->y1, K->y2, K->dO, K->dy, K->dy2})
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, act, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->o4, 0, sizeof(float) * 4 * cells, K->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(K->du, 0, sizeof(float) * 3 * cells, K->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(K->master, params, sizeof(float) * NP, cudaMemcpyHostToDevice, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->m, 0, sizeof(float) * NP, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->v, 0, sizeof(float) * NP, K->stream);
@@ -808,8 +828,10 @@ lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const ui
     if (!K || !rho || !u || !du) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = K->forward(mask, rho, u);
     const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
-    if (e == cudaSuccess) {
-        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, om, K->n_cells, K->du_scale, K->clip, du);
+    // the slabs write their cells; the rest of the caller's box is zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(du, 0, sizeof(float) * 3 * K->n_cells, K->stream);
+    if (e == cudaSuccess && K->n_slabs) {
+        k_output<<<(unsigned)K->n_slabs, 128, 0, K->stream>>>(K->o4, om, K->box, K->du_scale, K->clip, du, K->slabs);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector forward: ") + cudaGetErrorString(e));
@@ -875,9 +897,9 @@ lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t*
     if (s) return s;
     cudaError_t e = K->forward(mask, K->rho, K->u);
     const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
-    if (e == cudaSuccess) {
-        k_output<<<blocks(K->n_cells, 256), 256, 0, K->stream>>>(K->o4, om, K->n_cells, (float)(K->du_scale * gain),
-                                                                 K->clip, K->du);
+    if (e == cudaSuccess && K->n_slabs) {  // cells outside the slabs keep the zero of set-up
+        k_output<<<(unsigned)K->n_slabs, 128, 0, K->stream>>>(K->o4, om, K->box, (float)(K->du_scale * gain), K->clip,
+                                                              K->du, K->slabs);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector apply: ") + cudaGetErrorString(e));
