@@ -174,10 +174,21 @@ __device__ __forceinline__ void corner_slots(const int32_t* nb8, uint32_t slot, 
 
 // Esoteric twist read at level parity P: f_i from slot (P ? opp(i) : i) of cell x + p_opp(i);
 // on a wall link the other slot of the same cell, which holds f*_opp(i)(x, n - 1).
-template <int ST, bool RW>
+// PC >= 0 fixes the parity at compile time; with `clean` (warp-uniform: no lane of the warp has a
+// wall link) every plane index is then a constant.
+template <int ST, bool RW, int PC = -1>
 __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint32_t (&cs)[8], uint32_t wm,
-                                         int parity, float (&d)[Q])
+                                         int parity, float (&d)[Q], bool clean = false)
 {
+    if (PC >= 0 && clean) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t off = (PC ? (uint32_t)(Q - 1 - i) : (uint32_t)i) * n + cs[corner_neg(i)];
+            d[i] = RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off);
+        }
+        return;
+    }
+    if (PC >= 0) parity = PC;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const uint32_t flip = ((uint32_t)parity ^ (wm >> i)) & 1u;
@@ -187,11 +198,19 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
     }
 }
 
-// Esoteric twist write after a step of parity P: f*_i to slot (P ? i : opp(i)) of cell x + p_i.
-template <int ST>
+// Esoteric twist write after a step of parity P: f*_i to slot (P ? i : opp(i)) of cell x + p_i
+// (PC >= 0: the parity fixed at compile time).
+template <int ST, int PC = -1>
 __device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (&cs)[8], int parity,
                                          const float (&d)[Q])
 {
+    if (PC >= 0) {
+        parity = PC;
+        // with constant planes a write address equals the read address of the opposite
+        // direction; an opaque copy of n keeps the compiler from holding 27 addresses live
+        // through the collision (it recomputes them instead)
+        asm("mov.b32 %0, %0;" : "+r"(n));
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const uint32_t dir = parity ? (uint32_t)i : (uint32_t)(Q - 1 - i);
@@ -651,7 +670,7 @@ __device__ __forceinline__ void gather(const DomainView& v, const void* src, uin
 // ------------------------------------------------------------------------------ kernels
 // One fused update of the cell at `slot` (a lane of a warp that covers half of one brick; all
 // 32 lanes must call it together: the neighbour row goes round by shuffle).
-template <int ST, int SCHEME, int COLL>
+template <int ST, int SCHEME, int COLL, int PC = -1>
 __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, void* dst, const LevelArgs& a,
                                           uint32_t slot, uint32_t lane)
 {
@@ -667,11 +686,12 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         const int32_t row = __ldg(v.nb8 + brick * 8u + (lane & 7u));
         uint32_t cs[8];
         corner_slots_shfl(row, slot, cs);
+        const bool clean = PC >= 0 && __all_sync(0xffffffffu, wm == 0u);
         if (!fluid) return;
-        fetch_et<ST, true>(dst, n, cs, wm, a.parity, d);
+        fetch_et<ST, true, PC>(dst, n, cs, wm, a.parity, d, clean);
         const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
         collide_model<COLL>(d, la);
-        store_et<ST>(dst, n, cs, a.parity, d);
+        store_et<ST, PC>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
@@ -689,14 +709,14 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
     }
 }
 
-template <int ST, int SCHEME, int BRICKS, int MINB, int COLL>
+template <int ST, int SCHEME, int BRICKS, int MINB, int COLL, int PC = -1>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step(DomainView v, const void* src, void* dst, LevelArgs a)
 {
     const uint32_t slot = blockIdx.x * (uint32_t)(BRICKS * BRICK_CELLS) + threadIdx.x;
     // the active slots are a multiple of 64, so this exit is taken by whole warps
     if (slot >= (uint32_t)(v.n_bricks * BRICK_CELLS)) return;
-    step_cell<ST, SCHEME, COLL>(v, src, dst, a, slot, threadIdx.x & 31u);
+    step_cell<ST, SCHEME, COLL, PC>(v, src, dst, a, slot, threadIdx.x & 31u);
 }
 
 // Esoteric-twist step with two cells per thread: lane l of a warp updates cells l and l + 32 of
@@ -704,11 +724,11 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
 // FP32x2 instructions (the default rates only), which halves the issue slots of the arithmetic;
 // loads, wall rules and stores stay per cell.  A warp covers one brick, so the brick's corner
 // row still goes round by shuffle.  Results are bit-identical to the one-cell kernels.
-template <int ST>
+template <int ST, int PC>
 __device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop, const LevelArgs& a, uint32_t slot,
                                                  const uint32_t (&cs)[8], uint32_t half, const float (&d)[Q])
 {
-    store_et<ST>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
+    store_et<ST, PC>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
     if (half) {
         const uint32_t off = (uint32_t)v.aux[slot];
         const uint32_t wm = __ldg(v.word + slot) & WORD_WALL_MASK;
@@ -718,7 +738,7 @@ __device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop,
     }
 }
 
-template <int ST, int BRICKS, int MINB>
+template <int ST, int BRICKS, int MINB, int PC>
 __global__ void __launch_bounds__(BRICKS * 32, MINB)
     k_step2(DomainView v, void* pop, LevelArgs a)
 {
@@ -733,10 +753,11 @@ __global__ void __launch_bounds__(BRICKS * 32, MINB)
     corner_slots_shfl(row, slotB, csB);
     const uint32_t wA = __ldg(v.word + slotA), wB = __ldg(v.word + slotB);
     const bool fA = (wA & WORD_FLUID) != 0u, fB = (wB & WORD_FLUID) != 0u;
+    const bool clean = PC >= 0 && __all_sync(0xffffffffu, ((wA | wB) & WORD_WALL_MASK) == 0u);
     if (!fA && !fB) return;
     float dA[Q], dB[Q];
-    if (fA) fetch_et<ST, true>(pop, n, csA, wA & WORD_WALL_MASK, a.parity, dA);
-    if (fB) fetch_et<ST, true>(pop, n, csB, wB & WORD_WALL_MASK, a.parity, dB);
+    if (fA) fetch_et<ST, true, PC>(pop, n, csA, wA & WORD_WALL_MASK, a.parity, dA, clean);
+    if (fB) fetch_et<ST, true, PC>(pop, n, csB, wB & WORD_WALL_MASK, a.parity, dB, clean);
     const uint32_t halfA =
         (fA && (wA & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotA, wA, a, dA) : 0u;
     const uint32_t halfB =
@@ -750,12 +771,12 @@ __global__ void __launch_bounds__(BRICKS * 32, MINB)
     if (fA) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) dA[i] = d2[i].x;
-        store_twist_cell<ST>(v, pop, a, slotA, csA, halfA, dA);
+        store_twist_cell<ST, PC>(v, pop, a, slotA, csA, halfA, dA);
     }
     if (fB) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) dB[i] = d2[i].y;
-        store_twist_cell<ST>(v, pop, a, slotB, csB, halfB, dB);
+        store_twist_cell<ST, PC>(v, pop, a, slotB, csB, halfB, dB);
     }
 }
 
@@ -1128,7 +1149,14 @@ cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const
     if (v.n_bricks == 0) return cudaSuccess;
     const int grid = grid_for(v.n_bricks, BRICKS);
     return with_coll(a.coll, [&](auto c) {
-        k_step<ST, SCHEME, BRICKS, MINB, decltype(c)::value><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+        constexpr int C = decltype(c)::value;
+        // the twist with the default rates has one kernel per parity (constant plane indices)
+        if (SCHEME == LBM_SCHEME_ESOTERIC && C == COLL_CHM_FAST) {
+            if (a.parity) k_step<ST, SCHEME, BRICKS, MINB, C, 1><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+            else k_step<ST, SCHEME, BRICKS, MINB, C, 0><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+        } else {
+            k_step<ST, SCHEME, BRICKS, MINB, C><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
+        }
         return cudaGetLastError();
     });
 }
@@ -1137,7 +1165,9 @@ template <int ST, int BRICKS, int MINB>
 cudaError_t launch_step2(const DomainView& v, void* pop, const LevelArgs& a, cudaStream_t s)
 {
     if (v.n_bricks == 0) return cudaSuccess;
-    k_step2<ST, BRICKS, MINB><<<grid_for(v.n_bricks, BRICKS), BRICKS * 32, 0, s>>>(v, pop, a);
+    // runtime parity: the constant-plane form of the one-cell kernels was slower here (the two
+    // cells' addresses compete with the packed collision for the 128-register budget)
+    k_step2<ST, BRICKS, MINB, -1><<<grid_for(v.n_bricks, BRICKS), BRICKS * 32, 0, s>>>(v, pop, a);
     return cudaGetLastError();
 }
 
