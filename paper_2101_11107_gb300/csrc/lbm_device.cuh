@@ -58,9 +58,17 @@ struct Store<LBM_STORE_FP32> {
     {
         return __ldg(static_cast<const float*>(p) + off);
     }
+    // with a 256-byte L2 fetch on a miss: a warp reads 128 bytes of a brick's 256-byte plane
+    // row and the other half-brick warp (or the neighbour brick's shifted read) the rest, so
+    // the second request finds it in L2 (measured: -3% per step cold for the two-cell kernel,
+    // neutral to slightly worse for 16-bit storage, which keeps plain loads).  The asm is not
+    // volatile, so the compiler may schedule it freely: every caller's stores to a location it
+    // loaded depend on the loaded value.
     static __device__ __forceinline__ float load_rw(const void* p, int, uint32_t off)
     {
-        return static_cast<const float*>(p)[off];
+        float v;
+        asm("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(static_cast<const float*>(p) + off));
+        return v;
     }
     static __device__ __forceinline__ void store(void* p, int, uint32_t off, float v)
     {
