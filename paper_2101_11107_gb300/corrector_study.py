@@ -13,7 +13,10 @@ plain coarse run (u_c + du at the sample times), and in the loop, nudging the co
 50 steps with gain 1/4 after one period of warm-up (a full replacement every 50 steps, or nudges
 in a feedback loop at gain 1/2, destabilise the coarse run at tau ~ 0.503), falling back to the
 plain coarse solver if the state turns non-finite.  The corrector (3 conv layers, BF16 tensor cores) is trained on the
-GPU and applied every 50 coarse steps after one period of warm-up.  Evaluation on 8 held-out
+GPU and applied every 50 coarse steps after one period of warm-up.  Rounds of in-loop training
+(DAgger-style: the states a running corrector is applied to, paired with the restricted fine
+states at the same times, added to the training set) fit it to the states it meets in the
+loop.  Evaluation on 8 held-out
 geometries: relative L2 error of u against the restricted fine run over the coarse fluid cells
 at 10 phases of the last cycle, the similarity index of the paper's Sec. 3.4 (read with the
 factor 1/2 that bounds it by 1), and CUDA-event wall times of the fine, coarse and
@@ -58,7 +61,7 @@ def similarity_index(u_hr, u_lr, mask):
 
 
 def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples_per_period, train_steps, lr,
-        apply_every, workers, log, gain=0.25):
+        apply_every, workers, log, gain=0.25, dagger_rounds=0, dagger_steps=None):
     import torch
 
     from . import inputs as I
@@ -138,7 +141,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     union = np.zeros(pairs[train_seeds[0]][1].mask.shape, bool)
     for s in pairs:
         union |= pairs[s][1].mask > 0
-    masks, bulks, cells, data = {}, {}, {}, []
+    masks, bulks, cells, data, fine_targets = {}, {}, {}, [], {}
     t1 = time.time()
     for s in train_seeds:
         gf, gc = pairs[s]
@@ -148,8 +151,9 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         times = [t for t in range(apply_every, n_c + 1, apply_every) if t > n_c - 2 * period_c]
         for smp in simulate(gf, gc, times=times):
             idx = cells[s]
+            fine_targets[(s, smp["t"])] = smp["u_fine"].reshape(3, -1)[:, idx].clone()
             data.append((s, smp["rho"].reshape(-1)[idx].clone(), smp["u"].reshape(3, -1)[:, idx].clone(),
-                         smp["u_fine"].reshape(3, -1)[:, idx].clone()))
+                         fine_targets[(s, smp["t"])]))
     torch.cuda.synchronize()
     log(f"training data: {len(data)} samples from {len(train_seeds)} geometries in {time.time() - t1:.1f} s")
     shape = pairs[train_seeds[0]][1].mask.shape
@@ -172,18 +176,67 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
     net = lbm.Corrector(union.astype(np.uint8), I.corrector_init_params(0), U_SCALE, RHO_SCALE, DU_SCALE)
     rng = np.random.default_rng(0)
     losses = []
+
+    def train(n_steps, lr0):
+        for k in range(n_steps):
+            m, bm, rho, u, ut = dense(data[rng.integers(len(data))])
+            step_lr = lr0 if k < 0.7 * n_steps else lr0 * 0.2
+            losses.append(net.train_step(rho, u, ut, step_lr, mask=m, out_mask=bm))
+            if not np.isfinite(losses[-1]):
+                raise RuntimeError(f"training diverged at step {k}")
+
     torch.cuda.synchronize()
     t2 = time.time()
-    for k in range(train_steps):
-        m, bm, rho, u, ut = dense(data[rng.integers(len(data))])
-        step_lr = lr if k < 0.7 * train_steps else lr * 0.2
-        losses.append(net.train_step(rho, u, ut, step_lr, mask=m, out_mask=bm))
-        if not np.isfinite(losses[-1]):
-            raise RuntimeError(f"training diverged at step {k}")
+    train(train_steps, lr)
     torch.cuda.synchronize()
     train_s = time.time() - t2
     log(f"training: {train_steps} steps in {train_s:.1f} s, loss {np.mean(losses[:50]):.4f} -> "
         f"{np.mean(losses[-50:]):.4f}")
+
+    # ---------------------------------------------------------------- in-loop data (DAgger)
+    # The network is applied to states of a coarse run that it has already been correcting,
+    # which drift away from the plain coarse states it was trained on.  Each round runs the
+    # coarse solver of every training geometry with the current network in the loop, pairs the
+    # states it is applied to (before the correction) with the fine states restricted at the
+    # same times (the fine run does not depend on the network), adds them to the training set
+    # and trains on the union.
+    def coarse_in_loop(gc, times):
+        coarse = lbm.Domain.from_geometry(gc)
+        bc = lbm.Batch([coarse], graph_steps=apply_every)
+        cmask, bmask = tensors_mask(gc), bulk_mask(gc)
+        out = {}
+        for t in range(apply_every, n_c + 1, apply_every):
+            bc.step(apply_every)
+            if t in times:
+                out[t] = coarse.macroscopic_tensors()
+            if t >= apply_from:
+                net.apply(coarse, mask=cmask, out_mask=bmask, gain=gain)
+                if coarse.diagnostics(raise_unstable=False)["n_nonfinite"]:
+                    out = None
+                    break
+        bc.close()
+        return out
+
+    dagger_log = []
+    for rnd in range(dagger_rounds):
+        t3 = time.time()
+        added, unstable = 0, 0
+        for s in train_seeds:
+            states = coarse_in_loop(pairs[s][1], set(t for (s2, t) in fine_targets if s2 == s))
+            if states is None:
+                unstable += 1
+                continue
+            idx = cells[s]
+            for t, (rho, u) in states.items():
+                data.append((s, rho.reshape(-1)[idx].clone(), u.reshape(3, -1)[:, idx].clone(), fine_targets[(s, t)]))
+                added += 1
+        n_steps = dagger_steps if dagger_steps is not None else train_steps // 2
+        train(n_steps, lr * 0.5)
+        torch.cuda.synchronize()
+        dagger_log.append({"round": rnd + 1, "added": added, "unstable_runs": unstable, "train_steps": n_steps,
+                           "loss_last50": float(np.mean(losses[-50:])), "s": time.time() - t3})
+        log(f"in-loop round {rnd + 1}: {added} samples added ({unstable} unstable runs), {n_steps} steps, "
+            f"loss {np.mean(losses[-50:]):.4f}, {time.time() - t3:.1f} s")
 
     # ---------------------------------------------------------------- evaluation
     results = []
@@ -241,7 +294,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         "train_seeds": list(map(int, train_seeds)), "test_seeds": list(map(int, test_seeds)),
         "samples": len(data), "train_steps": train_steps, "train_s": train_s,
         "loss_first50": float(np.mean(losses[:50])), "loss_last50": float(np.mean(losses[-50:])),
-        "apply_every": apply_every, "gain": gain,
+        "apply_every": apply_every, "gain": gain, "dagger": dagger_log,
         "err_plain_mean": float(np.mean([r["err_plain"] for r in results])),
         "err_corrected_mean": float(np.mean([r["err_corrected"] for r in results])),
         "err_output_corrected_mean": float(np.mean([r["err_output_corrected"] for r in results])),
@@ -262,6 +315,9 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     ap.add_argument("--weights", default=None)
     ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--dagger", type=int, default=None,
+                    help="rounds of in-loop data collection and training (default 4; --small: 2)")
+    ap.add_argument("--gain", type=float, default=0.25)
     a = ap.parse_args(argv)
     if a.small:
         cfg = dict(fine_edge=128, period_f=800, reynolds=60.0, train_seeds=list(range(100, 116)),
@@ -270,7 +326,9 @@ def main(argv=None):
         cfg = dict(fine_edge=256, period_f=4000, reynolds=300.0, train_seeds=list(range(100, 132)),
                    test_seeds=list(range(200, 208)), periods=3, samples_per_period=10, train_steps=4000, lr=1e-3,
                    apply_every=50)
-    summary, net = run(workers=a.workers, log=lambda m: print(m, flush=True), **cfg)
+    dagger = a.dagger if a.dagger is not None else (2 if a.small else 4)
+    summary, net = run(workers=a.workers, log=lambda m: print(m, flush=True), dagger_rounds=dagger, gain=a.gain,
+                       **cfg)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(summary, f, indent=1)

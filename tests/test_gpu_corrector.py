@@ -155,14 +155,15 @@ def test_trained_corrector_gains_over_plain_coarse():
     coarse 64^3 synthetic aneurysms at Re 60, 16 training geometries, 2 held out), trained on the
     GPU by the corrector kernels.  On the held-out geometries the output-corrected coarse field
     is at least 5% closer (relative L2 of u against the restricted fine run) than the plain
-    coarse field, the in-loop run stays stable and within 1.5x of the plain error, and the
-    coarse + corrector run is faster than the fine run."""
+    coarse field, the in-loop run (after two rounds of in-loop training) stays stable and is
+    closer than the plain coarse run, and the coarse + corrector run is faster than the fine
+    run."""
     from paper_2101_11107_gb300 import corrector_study as S
 
     summary, _ = S.run(fine_edge=128, period_f=800, reynolds=60.0, train_seeds=list(range(100, 116)),
                        test_seeds=[200, 201], periods=3, samples_per_period=4, train_steps=1500, lr=2e-3,
-                       apply_every=50, workers=16, log=lambda m: None)
+                       apply_every=50, workers=16, log=lambda m: None, dagger_rounds=2)
     assert summary["err_output_corrected_mean"] < 0.95 * summary["err_plain_mean"], summary
-    assert summary["err_corrected_mean"] < 1.5 * summary["err_plain_mean"], summary
+    assert summary["err_corrected_mean"] < summary["err_plain_mean"], summary
     assert all(r["fallback_at_step"] is None for r in summary["per_geometry"])
     assert summary["wall_coarse_corrector_s"] < summary["wall_fine_s"]
