@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
 // Several domains (esoteric twist, one storage precision) in one launch: the CTAs run over the
 // concatenated brick lists; each warp finds its domain by binary search in the brick prefix
 // sums and updates one of that domain's half-bricks with the domain's own level arguments.
-template <int ST, int BRICKS, int MINB, int COLL>
+template <int ST, int BRICKS, int MINB, int COLL, int PC = -1>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step_batch(const BatchEntry* __restrict__ ent, const int64_t* __restrict__ brick_start, int n_dom,
                  const LevelArgs* __restrict__ args)
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     const DomainView v = ent[lo].view;
     const LevelArgs a = args[lo];
     const uint32_t slot = (uint32_t)((gbrick - __ldg(brick_start + lo)) * BRICK_CELLS) + (threadIdx.x & 63u);
-    step_cell<ST, LBM_SCHEME_ESOTERIC, COLL>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
+    step_cell<ST, LBM_SCHEME_ESOTERIC, COLL, PC>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
 }
 
 // Running means (the time averaging of Sec. 3.3): sums[k] += (rho, ux, uy, uz) of fluid cell k at
@@ -1159,7 +1159,7 @@ cudaError_t launch_step_t(const DomainView& v, const void* src, void* dst, const
     return with_coll(a.coll, [&](auto c) {
         constexpr int C = decltype(c)::value;
         // the twist with the default rates has one kernel per parity (constant plane indices)
-        if (SCHEME == LBM_SCHEME_ESOTERIC && C == COLL_CHM_FAST) {
+        if constexpr (SCHEME == LBM_SCHEME_ESOTERIC && C == COLL_CHM_FAST) {
             if (a.parity) k_step<ST, SCHEME, BRICKS, MINB, C, 1><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
             else k_step<ST, SCHEME, BRICKS, MINB, C, 0><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(v, src, dst, a);
         } else {
@@ -1312,27 +1312,37 @@ cudaError_t launch_apply_du(int scheme, const DomainView& v, void* pop, int pari
 
 template <int ST, int BRICKS, int MINB>
 cudaError_t launch_step_batch_t(const BatchEntry* ent, const int64_t* brick_start, int n_dom, int64_t total_bricks,
-                                const LevelArgs* args, int coll, cudaStream_t s)
+                                const LevelArgs* args, int coll, int parity, cudaStream_t s)
 {
     if (total_bricks == 0) return cudaSuccess;
     const int grid = grid_for(total_bricks, BRICKS);
     return with_coll(coll, [&](auto c) {
-        k_step_batch<ST, BRICKS, MINB, decltype(c)::value><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start,
-                                                                                              n_dom, args);
+        constexpr int C = decltype(c)::value;
+        // one kernel per parity when every domain has the same one (constant plane indices)
+        if constexpr (C == COLL_CHM_FAST) {
+            if (parity == 0)
+                k_step_batch<ST, BRICKS, MINB, C, 0><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
+            else if (parity == 1)
+                k_step_batch<ST, BRICKS, MINB, C, 1><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
+            else
+                k_step_batch<ST, BRICKS, MINB, C><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
+        } else {
+            k_step_batch<ST, BRICKS, MINB, C><<<grid, BRICKS * BRICK_CELLS, 0, s>>>(ent, brick_start, n_dom, args);
+        }
         return cudaGetLastError();
     });
 }
 
 template <int ST>
 cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
-                              int64_t total_bricks, const LevelArgs* args, int coll, cudaStream_t s)
+                              int64_t total_bricks, const LevelArgs* args, int coll, int parity, cudaStream_t s)
 {
     switch (config) {
-    case 0: return launch_step_batch_t<ST, 4, 3>(ent, brick_start, n_dom, total_bricks, args, coll, s);
-    case 1: return launch_step_batch_t<ST, 2, 7>(ent, brick_start, n_dom, total_bricks, args, coll, s);
-    case 2: return launch_step_batch_t<ST, 2, 6>(ent, brick_start, n_dom, total_bricks, args, coll, s);
-    case 3: return launch_step_batch_t<ST, 2, 8>(ent, brick_start, n_dom, total_bricks, args, coll, s);
-    default: return launch_step_batch_t<ST, 2, 10>(ent, brick_start, n_dom, total_bricks, args, coll, s);
+    case 0: return launch_step_batch_t<ST, 4, 3>(ent, brick_start, n_dom, total_bricks, args, coll, parity, s);
+    case 1: return launch_step_batch_t<ST, 2, 7>(ent, brick_start, n_dom, total_bricks, args, coll, parity, s);
+    case 2: return launch_step_batch_t<ST, 2, 6>(ent, brick_start, n_dom, total_bricks, args, coll, parity, s);
+    case 3: return launch_step_batch_t<ST, 2, 8>(ent, brick_start, n_dom, total_bricks, args, coll, parity, s);
+    default: return launch_step_batch_t<ST, 2, 10>(ent, brick_start, n_dom, total_bricks, args, coll, parity, s);
     }
 }
 

@@ -1042,9 +1042,18 @@ struct lbm_batch {
     size_t args_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     int exec_config = -1;
+    int exec_parity = -2;  // common parity of the captured chunk's first step (-1: mixed)
     cudaEvent_t ev = nullptr;
 
     int n() const { return (int)doms.size(); }
+    // the parity all domains have at step k of the argument table, or -1 if they differ
+    int common_parity(int k) const
+    {
+        const int p = h_args[(size_t)k * n()].parity;
+        for (int d = 1; d < n(); ++d)
+            if (h_args[(size_t)k * n() + d].parity != p) return -1;
+        return p;
+    }
     void fill_args(int steps)
     {
         for (int k = 0; k < steps; ++k)
@@ -1078,7 +1087,8 @@ struct lbm_batch {
                                         stream);
         const Launchers& L = launchers(storage);
         for (int k = 0; k < steps && e == cudaSuccess; ++k)
-            e = L.step_batch(config, d_ent, d_start, n(), total_bricks, d_args + (size_t)k * n(), coll, stream);
+            e = L.step_batch(config, d_ent, d_start, n(), total_bricks, d_args + (size_t)k * n(), coll,
+                             common_parity(k), stream);
         return e;
     }
     cudaError_t capture()
@@ -1096,6 +1106,7 @@ struct lbm_batch {
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
         exec_config = (e == cudaSuccess) ? launch_config : -1;
+        exec_parity = (e == cudaSuccess) ? common_parity(0) : -2;
         return e;
     }
     void release()
@@ -1193,7 +1204,10 @@ lbm_status lbm_batch_step(lbm_batch* B, int64_t n)
         if (e != cudaSuccess) break;
         B->fill_args(k);
         if (k == B->graph_steps) {
-            if (!B->exec || B->exec_config != B->launch_config) e = B->capture();
+            // the captured kernels are specialised by parity: recapture if the chunk starts
+            // with another one (an odd chunk length, or members stepped on their own)
+            if (!B->exec || B->exec_config != B->launch_config || B->exec_parity != B->common_parity(0))
+                e = B->capture();
             if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
         } else {
             e = B->enqueue_steps(k, B->launch_config);

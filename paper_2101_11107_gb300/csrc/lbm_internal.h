@@ -106,9 +106,11 @@ struct Launchers {
                                     const float* rho, const float* u, int64_t n_box, cudaStream_t stream);
     cudaError_t (*diagnostics)(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
                                const int32_t* fl_slot, int64_t n_fluid, double* partials, cudaStream_t stream);
-    // twist only: every domain of the batch one step; args[d] are domain d's level arguments
+    // twist only: every domain of the batch one step; args[d] are domain d's level arguments;
+    // parity: the parity every args[d].parity has (0 or 1), or -1 if they differ
     cudaError_t (*step_batch)(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
-                              int64_t total_bricks, const LevelArgs* args, int coll, cudaStream_t stream);
+                              int64_t total_bricks, const LevelArgs* args, int coll, int parity,
+                              cudaStream_t stream);
     // learned-corrector velocity shift of the post-collision populations of the previous level
     cudaError_t (*apply_du)(int scheme, const DomainView& v, void* pop, int parity_prev, const int32_t* fl_slot,
                             const int32_t* fl_box, int64_t n_fluid, const float* rho, const float* u, const float* du,
