@@ -74,6 +74,11 @@ struct Store<LBM_STORE_FP32> {
     {
         static_cast<float*>(p)[off] = v;
     }
+    // v carries the factor 2^nnz(c_i) of the deferred-halving inverse transform (exact)
+    static __device__ __forceinline__ void store_x(void* p, int i, uint32_t off, float v)
+    {
+        static_cast<float*>(p)[off] = nnz_of(i) ? v * pow2_neg(nnz_of(i)) : v;
+    }
 };
 
 template <>
@@ -91,6 +96,11 @@ struct Store<LBM_STORE_FP16> {
     {
         static_cast<__half*>(p)[off] = __float2half_rn(v * inv_w_of(i));
     }
+    // v carries the factor 2^nnz(c_i): one multiply by the exact constant 2^-nnz / w_i
+    static __device__ __forceinline__ void store_x(void* p, int i, uint32_t off, float v)
+    {
+        static_cast<__half*>(p)[off] = __float2half_rn(v * (inv_w_of(i) * pow2_neg(nnz_of(i))));
+    }
 };
 
 template <>
@@ -107,6 +117,10 @@ struct Store<LBM_STORE_BF16> {
     static __device__ __forceinline__ void store(void* p, int i, uint32_t off, float v)
     {
         static_cast<__nv_bfloat16*>(p)[off] = __float2bfloat16_rn(v * inv_w_of(i));
+    }
+    static __device__ __forceinline__ void store_x(void* p, int i, uint32_t off, float v)
+    {
+        static_cast<__nv_bfloat16*>(p)[off] = __float2bfloat16_rn(v * (inv_w_of(i) * pow2_neg(nnz_of(i))));
     }
 };
 
@@ -207,8 +221,8 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
 }
 
 // Esoteric twist write after a step of parity P: f*_i to slot (P ? i : opp(i)) of cell x + p_i
-// (PC >= 0: the parity fixed at compile time).
-template <int ST, int PC = -1>
+// (PC >= 0: the parity fixed at compile time; X: d carries the factors 2^nnz(c_i)).
+template <int ST, int PC = -1, bool X = false>
 __device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (&cs)[8], int parity,
                                          const float (&d)[Q])
 {
@@ -222,7 +236,8 @@ __device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const uint32_t dir = parity ? (uint32_t)i : (uint32_t)(Q - 1 - i);
-        Store<ST>::store(pop, i, dir * n + cs[corner_pos(i)], d[i]);
+        if (X) Store<ST>::store_x(pop, i, dir * n + cs[corner_pos(i)], d[i]);
+        else Store<ST>::store(pop, i, dir * n + cs[corner_pos(i)], d[i]);
     }
 }
 
@@ -469,7 +484,13 @@ struct Lane2 {
     static __device__ __forceinline__ V one_plus(V x) { return __fadd2_rn(make_float2(1.0f, 1.0f), x); }
 };
 
-template <class L>
+// 1-D inverse: (m0, m1, m2) -> (g(-1), g(0), g(+1)).  DEFER leaves out the halving of
+// g(+-1): the outputs at +-1 come out doubled, exactly (a power of two), and since the three
+// inputs of every later 1-D inverse share one such factor, each post-collision d_i leaves the
+// three passes multiplied by 2^nnz(c_i), which the store removes (Store::store_x) -- for 16-bit
+// storage inside the multiply by 1/w_i that it does anyway.  Bit-identical results, two fewer
+// instructions per 1-D inverse.
+template <class L, bool DEFER = false>
 __device__ __forceinline__ void inv3_t(typename L::V& m0, typename L::V& m1, typename L::V& m2, typename L::V u,
                                        typename L::V u2pcs, typename L::V two_u)
 {
@@ -477,12 +498,17 @@ __device__ __forceinline__ void inv3_t(typename L::V& m0, typename L::V& m1, typ
     const V S1 = L::fma(u, m0, m1);
     const V S2 = L::fma(u2pcs, m0, L::fma(two_u, m1, m2));
     const V g0 = L::sub(m0, S2);
-    m0 = L::mul(L::splat(0.5f), L::sub(S2, S1));
-    m2 = L::mul(L::splat(0.5f), L::add(S2, S1));
+    if (DEFER) {
+        m0 = L::sub(S2, S1);
+        m2 = L::add(S2, S1);
+    } else {
+        m0 = L::mul(L::splat(0.5f), L::sub(S2, S1));
+        m2 = L::mul(L::splat(0.5f), L::add(S2, S1));
+    }
     m1 = g0;
 }
 
-template <class L>
+template <class L, bool DEFER = false>
 __device__ __forceinline__ void collide_fast_t(typename L::V (&d)[Q], typename L::V s2, const float g[3])
 {
     using V = typename L::V;
@@ -559,16 +585,20 @@ __device__ __forceinline__ void collide_fast_t(typename L::V (&d)[Q], typename L
 #pragma unroll
     for (int q = 0; q < 3; ++q)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) inv3_t<L>(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, zc, z2);
+        for (int p = 0; p < 3; ++p) inv3_t<L, DEFER>(d[p + 3 * q], d[p + 3 * q + 9], d[p + 3 * q + 18], uz, zc, z2);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) inv3_t<L>(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, yc, y2);
+        for (int p = 0; p < 3; ++p) inv3_t<L, DEFER>(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, yc, y2);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) inv3_t<L>(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, xc, x2);
+    for (int k = 0; k < 9; ++k) inv3_t<L, DEFER>(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, xc, x2);
 }
 
-__device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a) { collide_fast_t<Lane1>(d, a.s2, a.g); }
+template <bool DEFER = false>
+__device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a)
+{
+    collide_fast_t<Lane1, DEFER>(d, a.s2, a.g);
+}
 
 // The classical operators the paper compares against (Sec. 2.1.2), with the second-order
 // equilibrium f_eq2_i = w_i rho [1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u] and the second-order (Guo)
@@ -639,10 +669,12 @@ __device__ __forceinline__ void collide_trt2(float (&d)[Q], const LevelArgs& a)
     d[13] += drho - pm;
 }
 
-template <int COLL>
+// DEFER (the default rates only): d leaves with the factors 2^nnz(c_i), for Store::store_x
+template <int COLL, bool DEFER = false>
 __device__ __forceinline__ void collide_model(float (&d)[Q], const LevelArgs& a)
 {
-    if (COLL == COLL_CHM_FAST) collide_fast(d, a);
+    static_assert(!DEFER || COLL == COLL_CHM_FAST, "deferred halving is a form of the fast collision");
+    if (COLL == COLL_CHM_FAST) collide_fast<DEFER>(d, a);
     else if (COLL == COLL_CHM) collide(d, a);
     else collide_trt2<COLL == COLL_TRT2>(d, a);
 }
@@ -682,6 +714,7 @@ template <int ST, int SCHEME, int COLL, int PC = -1>
 __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, void* dst, const LevelArgs& a,
                                           uint32_t slot, uint32_t lane)
 {
+    constexpr bool X = COLL == COLL_CHM_FAST;  // deferred halving in the inverse transform
     const uint32_t brick = slot / BRICK_CELLS;
     const uint32_t word = __ldg(v.word + slot);
     const bool fluid = (word & WORD_FLUID) != 0u;
@@ -698,22 +731,28 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         if (!fluid) return;
         fetch_et<ST, true, PC>(dst, n, cs, wm, a.parity, d, clean);
         const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
-        collide_model<COLL>(d, la);
-        store_et<ST, PC>(dst, n, cs, a.parity, d);
+        collide_model<COLL, X>(d, la);
+        store_et<ST, PC, X>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if (half & (1u << i)) Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
+                if (half & (1u << i)) {
+                    if (X) Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
+                    else Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
+                }
         }
     } else {
         const int32_t row = __ldg(v.nbr + brick * (uint32_t)Q + (lane < (uint32_t)Q ? lane : 0u));
         fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
         if (!fluid) return;
         if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
-        collide_model<COLL>(d, la);
+        collide_model<COLL, X>(d, la);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
+        for (int i = 0; i < Q; ++i) {
+            if (X) Store<ST>::store_x(dst, i, (uint32_t)i * n + slot, d[i]);
+            else Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
+        }
     }
 }
 
@@ -736,13 +775,13 @@ template <int ST, int PC>
 __device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop, const LevelArgs& a, uint32_t slot,
                                                  const uint32_t (&cs)[8], uint32_t half, const float (&d)[Q])
 {
-    store_et<ST, PC>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
+    store_et<ST, PC, true>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
     if (half) {
         const uint32_t off = (uint32_t)v.aux[slot];
         const uint32_t wm = __ldg(v.word + slot) & WORD_WALL_MASK;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            if (half & (1u << i)) Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
+            if (half & (1u << i)) Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
     }
 }
 
@@ -775,7 +814,7 @@ __global__ void __launch_bounds__(BRICKS * 32, MINB)
     float2 d2[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d2[i] = make_float2(fA ? dA[i] : 0.0f, fB ? dB[i] : 0.0f);  // a solid lane: rest
-    collide_fast_t<Lane2>(d2, make_float2(s2A, s2B), a.g);
+    collide_fast_t<Lane2, true>(d2, make_float2(s2A, s2B), a.g);  // stores through Store::store_x
     if (fA) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) dA[i] = d2[i].x;

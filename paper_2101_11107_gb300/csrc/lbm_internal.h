@@ -21,6 +21,9 @@ __host__ __device__ constexpr float w_of(int i)
     return w1_of(cx_of(i)) * w1_of(cy_of(i)) * w1_of(cz_of(i));
 }
 __host__ __device__ constexpr float inv_w_of(int i) { return 1.0f / w_of(i); }
+// number of nonzero components of c_i, and 2^-k
+__host__ __device__ constexpr int nnz_of(int i) { return (cx_of(i) != 0) + (cy_of(i) != 0) + (cz_of(i) != 0); }
+__host__ __device__ constexpr float pow2_neg(int k) { return k == 0 ? 1.0f : k == 1 ? 0.5f : k == 2 ? 0.25f : 0.125f; }
 // corner of the positive part p_i = max(c_i, 0), and of p_opp(i) = max(-c_i, 0): e = px + 2py + 4pz
 __host__ __device__ constexpr int corner_pos(int i) { return (cx_of(i) > 0) + 2 * (cy_of(i) > 0) + 4 * (cz_of(i) > 0); }
 __host__ __device__ constexpr int corner_neg(int i) { return (cx_of(i) < 0) + 2 * (cy_of(i) < 0) + 4 * (cz_of(i) < 0); }
