@@ -44,8 +44,8 @@ BYTES_PER_VALUE = {"fp32": 4, "fp16": 2, "bf16": 2}
 # configuration, from the ncu captures summarised in profiles/ (dram__bytes_read.sum +
 # dram__bytes_write.sum); reported only for the configuration the bench runs
 K_STEP_TRAFFIC = {
-    "128x6": (98_139_904, "profiles/k_step_womersley_fp32_twist.md"),      # 79.99 + 18.15 MB
-    "2c128x4": (98_178_816, "profiles/k_step2_womersley_fp32_twist.md"),   # 80.03 + 18.15 MB
+    "128x6": (98_186_752, "profiles/k_step_womersley_fp32_twist.md"),      # 80.00 + 18.19 MB
+    "2c128x4": (97_849_088, "profiles/k_step2_womersley_fp32_twist.md"),   # 80.03 + 17.82 MB
 }
 
 
