@@ -248,7 +248,10 @@ lbm_status lbm_autotune(lbm_domain* dom, int32_t trial_steps, int32_t* best_conf
  *     later.  Small tables are allocated through doms[0]'s allocator.  Errors: INVALID_ARG, OOM,
  *     CUDA.
  *   lbm_batch_step: n >= 0 steps of every domain (each domain's time advances by n); waits for
- *     the previous chunk before refilling its host argument table.
+ *     the previous chunk before refilling its host argument table.  When all domains share
+ *     one time parity the captured kernels are specialised for it; the graph is captured again
+ *     whenever a chunk starts with another parity pattern than the captured one (an odd
+ *     graph_steps does this every chunk: prefer an even one).
  *   lbm_batch_set_launch_config / lbm_batch_autotune: as for single domains (the batched kernel
  *     has configurations 0-4; the others run as 4, and autotune does not time them); autotune
  *     keeps every domain's state (it copies and restores the populations) and needs trial_steps
