@@ -564,6 +564,7 @@ struct lbm_corrector {
     int4* slabs = nullptr;   // 8 x 16 x 1 slabs covering those tiles (convolutions)
     int64_t n_slabs = 0;
     unsigned int* err = nullptr;  // set by a conv CTA whose bounded wait gave up
+    cudaEvent_t ev = nullptr;     // orders the corrector's stream and a domain's stream (apply)
     CUtensorMap tmaps[5];         // halo maps of x0, y1, y2, dO, dy2 (the convolutions' inputs)
     const void* tmap_of[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     __nv_bfloat16 *x0 = nullptr, *y1 = nullptr, *y2 = nullptr, *dO = nullptr, *dy = nullptr, *dy2 = nullptr;
@@ -589,6 +590,8 @@ struct lbm_corrector {
     }
     void release_all()
     {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
         for (void* p : owned) {
             if (release) release(p, ctx);
             else if (!alloc) cudaFree(p);
@@ -775,6 +778,7 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
     if (e == cudaSuccess && !sv.empty())
         e = cudaMemcpyAsync(K->slabs, sv.data(), sizeof(int4) * sv.size(), cudaMemcpyHostToDevice, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->err, 0, sizeof(unsigned int), K->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&K->ev, cudaEventDisableTiming);
     {
         const __nv_bfloat16* ins[5] = {K->x0, K->y1, K->y2, K->dO, K->dy2};
         for (int t = 0; t < 5 && e == cudaSuccess; ++t) {
@@ -893,14 +897,27 @@ lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t*
     lbm_get_info(dom, &I);
     if (I.nx != K->box.nx || I.ny != K->box.ny || I.nz != K->box.nz)
         return nn_fail(LBM_ERR_INVALID_ARG, "the domain's box differs from the corrector's");
+    DomainAccess da{};
+    if (!domain_access(dom, &da)) return nn_fail(LBM_ERR_INVALID_ARG, "NULL domain");
+    // rho, u are exported on the domain's stream and the correction is applied there: the
+    // corrector's own stream waits for the one and the domain's stream for the other
     lbm_status s = lbm_get_macroscopic(dom, K->rho, K->u, 1, 1);
     if (s) return s;
-    cudaError_t e = K->forward(mask, K->rho, K->u);
+    cudaError_t e = cudaSuccess;
+    if (da.stream != K->stream) {
+        e = cudaEventRecord(K->ev, da.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(K->stream, K->ev, 0);
+    }
+    if (e == cudaSuccess) e = K->forward(mask, K->rho, K->u);
     const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
     if (e == cudaSuccess && K->n_slabs) {  // cells outside the slabs keep the zero of set-up
         k_output<<<(unsigned)K->n_slabs, 128, 0, K->stream>>>(K->o4, om, K->box, (float)(K->du_scale * gain), K->clip,
                                                               K->du, K->slabs);
         e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && da.stream != K->stream) {
+        e = cudaEventRecord(K->ev, K->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(da.stream, K->ev, 0);
     }
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector apply: ") + cudaGetErrorString(e));
     return lbm_apply_velocity_correction(dom, K->du, 1);

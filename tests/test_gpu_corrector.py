@@ -150,6 +150,26 @@ def test_apply_through_corrector():
     assert np.array_equal(a.macroscopic()[1], b.macroscopic()[1])
 
 
+def test_apply_with_the_domain_and_the_corrector_on_different_streams():
+    """The domain's work on one stream, the corrector's on another: the apply orders the two
+    (export -> network -> correction) and gives the same fields as with one stream."""
+    import torch
+
+    g = I.aneurysm(9, edge=64, period=200.0, reynolds=30.0)
+    params = I.corrector_init_params(2)
+    s_dom, s_net = torch.cuda.Stream(), torch.cuda.Stream()
+    a = lbm.Domain.from_geometry(g, stream=s_dom)
+    b = lbm.Domain.from_geometry(g)
+    net_a = lbm.Corrector(g.mask, params, US, RS, DS, stream=s_net)
+    net_b = lbm.Corrector(g.mask, params, US, RS, DS)
+    for _ in range(3):
+        a.step(20)
+        b.step(20)
+        net_a.apply(a, gain=0.5)
+        net_b.apply(b, gain=0.5)
+    assert np.array_equal(a.macroscopic()[1], b.macroscopic()[1])
+
+
 def test_trained_corrector_gains_over_plain_coarse():
     """What the trained network gains over the method without it: the small study (fine 128^3 /
     coarse 64^3 synthetic aneurysms at Re 60, 16 training geometries, 2 held out), trained on the
