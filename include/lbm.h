@@ -294,7 +294,10 @@ void lbm_batch_destroy(lbm_batch* batch);
  *   lbm_apply_velocity_correction: the post-collision populations of the previous level gain
  *     f_eq(rho, u + du) - f_eq(rho, u) at every fluid cell except inlet and outlet cells (whose
  *     unknowns the closures rebuild each step; rho, u of the current level); du are
- *     three planes on the dense box (host or device pointers); waits.
+ *     three planes on the dense box (host or device pointers); waits for host pointers, and
+ *     with device pointers is enqueued on the domain's stream (du must stay valid until that
+ *     work has run).  The first call allocates a staging buffer of 7 planes that the domain
+ *     keeps.
  *   lbm_restrict: coarse rho, u (dense, device) = mean over the fluid children of each coarse
  *     cell of the fine dense fields (fine extents even; fine_mask nonzero = fluid, device).
  * All device pointers belong to the caller.  Errors: INVALID_ARG, OOM, CUDA.

@@ -61,6 +61,7 @@ struct lbm_domain {
     void* alloc_ctx = nullptr;
     std::vector<void*> owned;
     int64_t device_bytes = 0;
+    float* d_corr_stage = nullptr;  // rho, u and a staged du for the velocity correction (lazy)
     // host copies kept for checkpoints
     uint64_t geometry_hash = 0;
 
@@ -829,9 +830,13 @@ lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t
     g_last_error.clear();
     if (!D || !du) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
     const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
-    const size_t bytes = sizeof(float) * (size_t)(device_ptrs ? 4 : 7) * (size_t)std::max<int64_t>(n_box, 1);
-    float* stage = static_cast<float*>(D->dev_alloc(bytes));
-    if (!stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+    // one staging buffer per domain, kept: the correction runs every few dozen steps, and the
+    // work of successive calls is ordered on the domain's stream
+    if (!D->d_corr_stage) {
+        D->d_corr_stage = static_cast<float*>(D->dev_alloc(sizeof(float) * 7 * (size_t)std::max<int64_t>(n_box, 1)));
+        if (!D->d_corr_stage) return fail(LBM_ERR_OOM, "allocation failed: staging");
+    }
+    float* stage = D->d_corr_stage;
     float* rho = stage;
     float* u = stage + n_box;
     const float* dd = du;
@@ -848,9 +853,10 @@ lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t
     if (e == cudaSuccess)
         e = L.apply_du(D->params.scheme, D->view, D->src(), (int)((D->time + 1) & 1), D->d_fl_slot, D->d_fl_box,
                        D->n_fluid, rho, u, dd, n_box, D->stream);
-    cudaError_t e2 = cudaStreamSynchronize(D->stream);
-    if (e == cudaSuccess) e = e2;
-    D->dev_free(stage, bytes);
+    if (!device_ptrs) {  // the host array may be reused as soon as the call returns
+        cudaError_t e2 = cudaStreamSynchronize(D->stream);
+        if (e == cudaSuccess) e = e2;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "velocity correction");
     return LBM_OK;
 }

@@ -375,12 +375,14 @@ class Domain:
 
     def apply_velocity_correction(self, du):
         """Post-collision populations of the previous level += f_eq(rho, u + du) - f_eq(rho, u);
-        du: (3, nz, ny, nx) numpy array or CUDA tensor."""
+        du: (3, nz, ny, nx) numpy array (the call waits) or CUDA tensor (enqueued on the domain's
+        stream)."""
         import torch
         L = load_library()
         if isinstance(du, torch.Tensor):
             t = du.to(torch.float32).contiguous()
             _check(L.lbm_apply_velocity_correction(self._h, ctypes.c_void_p(t.data_ptr()), 1))
+            t.record_stream(self.stream)  # keep t's memory until the domain's stream has read it
         else:
             a = np.ascontiguousarray(du, dtype=np.float32)
             _check(L.lbm_apply_velocity_correction(self._h, _ptr(a), 0))
