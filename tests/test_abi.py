@@ -68,8 +68,9 @@ def _create(L, mask, links=None, params=None, inlet_center=None, inlet_radius=0.
     return st, L.lbm_last_error().decode(), h
 
 
-@pytest.mark.parametrize("case", ["mask_value", "periodic_extent", "tau", "omega", "link_not_wall",
-                                  "link_q", "link_on_inlet", "duplicate_link", "open_cell_off_face",
+@pytest.mark.parametrize("case", ["mask_value", "periodic_extent", "tau", "tau_nan", "omega", "link_not_wall",
+                                  "link_q", "link_q_nan", "link_q_above_one", "link_rest_direction",
+                                  "link_on_inlet", "duplicate_link", "open_cell_off_face",
                                   "inlet_without_radius", "collision", "trt_magic"])
 def test_invalid_arguments_rejected_before_device_work(L, case):
     mask = np.ones((4, 8, 8), np.uint8)
@@ -83,12 +84,20 @@ def test_invalid_arguments_rejected_before_device_work(L, case):
         kw["params"] = {"periodic": (1, 1, 1)}
     elif case == "tau":
         kw["params"] = {"tau": 0.5}
+    elif case == "tau_nan":
+        kw["params"] = {"tau": float("nan")}
     elif case == "omega":
         kw["params"] = {"omega_hi": (ctypes.c_double * 4)(1.0, 2.5, 1.0, 1.0)}
     elif case == "link_not_wall":
         kw["links"] = ([1 + 8 * 2 + 64 * 1], [14], [0.3])  # +x neighbour of (1,2,1) is fluid
     elif case == "link_q":
         kw["links"] = ([1 + 8 * 2 + 64 * 1], [12], [0.0])
+    elif case == "link_q_nan":
+        kw["links"] = ([1 + 8 * 2 + 64 * 1], [12], [float("nan")])
+    elif case == "link_q_above_one":
+        kw["links"] = ([1 + 8 * 2 + 64 * 1], [12], [1.5])
+    elif case == "link_rest_direction":
+        kw["links"] = ([1 + 8 * 2 + 64 * 1], [13], [0.3])
     elif case == "link_on_inlet":
         mask[:, :, 1] = 2
         kw["links"] = ([1 + 8 * 2 + 64 * 1], [12], [0.3])
