@@ -134,3 +134,41 @@ def test_domain_beyond_the_32_bit_offset_range_is_rejected(L):
     mask = np.ones((544, 544, 544), np.uint8)
     st, msg, h = _create(L, mask, params={"periodic": (1, 1, 1)})
     assert st == 1 and "too large" in msg and not h.value
+
+
+def test_batch_corrector_and_restriction_reject_invalid_arguments(L):
+    """Entry points beyond the domain refuse bad arguments before any device work (INVALID_ARG,
+    no handle written)."""
+    out = ctypes.c_void_p(123)
+    assert L.lbm_batch_create(None, 0, 10, None, ctypes.byref(out)) == 1 and not out.value
+    members = (ctypes.c_void_p * 1)(None)
+    out = ctypes.c_void_p(123)
+    assert L.lbm_batch_create(members, 1, 0, None, ctypes.byref(out)) == 1  # graph_steps out of range
+    assert "graph_steps" in L.lbm_last_error().decode() and not out.value
+    out = ctypes.c_void_p(123)
+    assert L.lbm_batch_create(members, 1, 10, None, ctypes.byref(out)) == 1  # NULL member
+    assert not out.value
+
+    assert L.lbm_corrector_num_params() == 3 * (27 * 16 * 16 + 16)
+    params = np.zeros(L.lbm_corrector_num_params(), np.float32)
+
+    def corrector(nx, ny, nz, scales=(0.05, 0.01, 0.005), alloc=None, free=None):
+        mask = np.ones((nz, ny, nx), np.uint8)
+        h = ctypes.c_void_p(123)
+        st = L.lbm_corrector_create(lbm._ptr(mask), nx, ny, nz, *scales, lbm._ptr(params),
+                                    alloc if alloc is not None else lbm.ALLOC_FN(0),
+                                    free if free is not None else lbm.FREE_FN(0), None, None, ctypes.byref(h))
+        return st, L.lbm_last_error().decode(), h
+
+    st, msg, h = corrector(10, 8, 8)
+    assert st == 1 and "multiples of 4" in msg and not h.value
+    st, msg, h = corrector(8, 8, 8, scales=(0.05, 0.0, 0.005))
+    assert st == 1 and "scales" in msg and not h.value
+    st, msg, h = corrector(8, 8, 8, alloc=lbm.ALLOC_FN(lambda n, c: None))
+    assert st == 1 and "allocator" in msg and not h.value
+
+    buf = np.zeros(64, np.float32)
+    fm = np.ones(64, np.uint8)
+    assert L.lbm_restrict(lbm._ptr(buf), lbm._ptr(buf), lbm._ptr(fm), 3, 4, 4, lbm._ptr(buf), lbm._ptr(buf),
+                          None) == 1
+    assert L.lbm_restrict(None, lbm._ptr(buf), lbm._ptr(fm), 4, 4, 4, lbm._ptr(buf), lbm._ptr(buf), None) == 1
