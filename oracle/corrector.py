@@ -110,9 +110,11 @@ def loss_and_grad(x0, target, mask, params):
 
 
 def correction(x0, mask, params, du_scale, clip=2.0):
-    """du = du_scale * clamp(O[0:3], -clip, clip) at fluid cells."""
+    """du = du_scale * clamp(O[0:3], -clip, clip) at fluid cells, exactly 0 elsewhere.  The
+    clamp acts on the network output O (in units of du_scale), not on du; a non-finite O stays
+    non-finite (np.clip passes NaN through)."""
     o, _ = forward(x0, params)
-    return du_scale * np.clip(o[0:3], -clip, clip) * (mask > 0)
+    return np.where(mask > 0, du_scale * np.clip(o[0:3], -clip, clip), 0.0)
 
 
 def restrict(fine, fine_mask):

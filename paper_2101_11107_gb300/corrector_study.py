@@ -52,6 +52,20 @@ def geometry_pairs(seeds, fine_edge, period_f, reynolds, workers):
     return {s: (gf, gc) for s, gf, gc in out}
 
 
+def correct_or_fall_back(coarse, corrector, mask, out_mask, gain):
+    """One in-loop correction of a running coarse domain, with the plain solver as fallback:
+    the corrector nudges the domain's state; if the corrected state has a non-finite cell (FP64
+    diagnostics count), the domain is put back to the macroscopic state it had before the
+    correction (populations re-initialised at equilibrium from that rho and u) and False is
+    returned, after which the caller runs the plain solver.  True: the correction was kept."""
+    rho0, u0 = coarse.macroscopic_tensors()
+    corrector.apply(coarse, mask=mask, out_mask=out_mask, gain=gain)
+    if coarse.diagnostics(raise_unstable=False)["n_nonfinite"]:
+        coarse.init_equilibrium(rho0, u0)
+        return False
+    return True
+
+
 def similarity_index(u_hr, u_lr, mask):
     """Similarity index of Sec. 3.4 (factor 1/2) over the cells where mask != 0, computed on the
     device by lbm_similarity_index; u_hr, u_lr CUDA tensors (3, nz, ny, nx), mask a CUDA tensor."""
@@ -116,10 +130,7 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             bf.step(2 * apply_every)
             bc.step(apply_every)
             if corrector is not None and state["fallback"] is None and t >= apply_from:
-                rho0, u0 = coarse.macroscopic_tensors()
-                corrector.apply(coarse, mask=cmask, out_mask=bmask, gain=gain)
-                if coarse.diagnostics(raise_unstable=False)["n_nonfinite"]:
-                    coarse.init_equilibrium(rho0, u0)
+                if not correct_or_fall_back(coarse, corrector, cmask, bmask, gain):
                     state["fallback"] = t
             if t in times:
                 fr, fu = fine.macroscopic_tensors()

@@ -397,7 +397,15 @@ __global__ void __launch_bounds__(128) k_features(const float* __restrict__ rho,
 }
 
 // du = du_scale * clamp(O[0:3], -clip, clip) at the masked cells of the slabs, 0 at their other
-// cells (three planes; the caller zeroes the rest of the box).
+// cells (three planes; the caller zeroes the rest of the box).  The clamp lets a NaN through
+// (fminf/fmaxf would turn it into -clip): a network that has gone non-finite must make the
+// corrected state non-finite, which the caller's fallback detects, not apply a full-size
+// correction everywhere.
+__device__ __forceinline__ float clamp_keep_nan(float o, float clip)
+{
+    return o > clip ? clip : (o < -clip ? -clip : o);
+}
+
 __global__ void __launch_bounds__(128) k_output(const float* __restrict__ o4, const uint8_t* __restrict__ mask, Box b,
                                                 float du_scale, float clip, float* __restrict__ du,
                                                 const int4* __restrict__ slabs)
@@ -406,10 +414,10 @@ __global__ void __launch_bounds__(128) k_output(const float* __restrict__ o4, co
     int64_t c;
     if (!slab_cell(slabs, b, x, y, z, c)) return;
     const int64_t n = (int64_t)b.nx * b.ny * b.nz;
-    const float fl = mask[c] ? du_scale : 0.0f;
-    du[c] = fminf(fmaxf(o4[c * 4 + 0], -clip), clip) * fl;
-    du[n + c] = fminf(fmaxf(o4[c * 4 + 1], -clip), clip) * fl;
-    du[2 * n + c] = fminf(fmaxf(o4[c * 4 + 2], -clip), clip) * fl;
+    const bool on = mask[c] != 0;
+    du[c] = on ? clamp_keep_nan(o4[c * 4 + 0], clip) * du_scale : 0.0f;
+    du[n + c] = on ? clamp_keep_nan(o4[c * 4 + 1], clip) * du_scale : 0.0f;
+    du[2 * n + c] = on ? clamp_keep_nan(o4[c * 4 + 2], clip) * du_scale : 0.0f;
 }
 
 // Loss = mean over fluid cells and components of (O - T)^2, T = (u_target - u) / du_scale;

@@ -75,3 +75,46 @@ def test_features_zero_at_solid():
     x = K.features(np.full(mask.shape, 1.02), np.full((3,) + mask.shape, 0.01), mask, 0.05, 0.01)
     assert x[0, 1, 1, 1] == pytest.approx(0.2) and x[3, 1, 1, 1] == pytest.approx(2.0)
     assert np.count_nonzero(x[:, 0, 0, 0]) == 0 and np.all(x[5:] == 0) and x[4].sum() == 1
+
+
+def _constant_output_params(b3):
+    """Parameters whose network output is the constant b3 everywhere (W3 = 0)."""
+    params = I.corrector_init_params(1)
+    params[4] = np.zeros_like(params[4])
+    params[5] = np.asarray(b3, dtype=np.float64)
+    return params
+
+
+def test_correction_clamps_the_network_output_not_du():
+    """O = (5, -5, 0.5, ...) everywhere: with du_scale 0.005 and clip 2 the correction is
+    (0.01, -0.01, 0.0025) at fluid cells and exactly 0 elsewhere.  A clamp applied to du instead
+    of O (at +-2) would leave 0.025 and -0.025; a clamp on O alone with the wrong sign or a
+    missing du_scale would give other values."""
+    mask = np.zeros((4, 5, 6), np.uint8)
+    mask[1:3, 1:4, 2:5] = 1
+    b3 = np.zeros(16)
+    b3[:3] = [5.0, -5.0, 0.5]
+    x0 = K.features(np.ones(mask.shape), np.zeros((3,) + mask.shape), mask, 0.05, 0.01)
+    du = K.correction(x0, mask, _constant_output_params(b3), 0.005)
+    fl = mask > 0
+    assert np.all(du[0][fl] == 0.005 * 2.0) and np.all(du[1][fl] == -0.005 * 2.0)
+    assert np.allclose(du[2][fl], 0.005 * 0.5, rtol=0, atol=1e-18)
+    assert np.all(du[:, ~fl] == 0.0)
+    # inside the bounds the output passes unchanged: O = 1.999 -> du = 0.005 * 1.999
+    b3[:3] = [1.999, -1.999, 0.0]
+    du = K.correction(x0, mask, _constant_output_params(b3), 0.005)
+    assert np.allclose(du[0][fl], 0.005 * 1.999, rtol=1e-15) and np.allclose(du[1][fl], -0.005 * 1.999, rtol=1e-15)
+    assert np.all(du[2][fl] == 0.0)
+
+
+def test_correction_keeps_a_non_finite_output_non_finite():
+    """A network that has gone non-finite gives a non-finite correction at fluid cells (so that
+    the corrected state is flagged and the plain solver takes over), and still 0 elsewhere."""
+    mask = np.zeros((4, 4, 4), np.uint8)
+    mask[1:3, 1:3, 1:3] = 1
+    b3 = np.zeros(16)
+    b3[0] = np.nan
+    x0 = K.features(np.ones(mask.shape), np.zeros((3,) + mask.shape), mask, 0.05, 0.01)
+    du = K.correction(x0, mask, _constant_output_params(b3), 0.005)
+    fl = mask > 0
+    assert np.all(np.isnan(du[0][fl])) and np.all(du[0][~fl] == 0.0) and np.all(du[1:] == 0.0)

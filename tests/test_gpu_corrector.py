@@ -44,6 +44,49 @@ def _case(n=16, seed=0):
     return mask, rho, u, ut, params
 
 
+def _multi_slab_case(seed=0):
+    """A 48 x 64 x 64 box (x, y, z) holding an ellipsoidal vessel with a cylindrical obstacle:
+    1504 slabs of 8 x 16 x 1 cells and 2688 active 4^3 tiles, so that every persistent CTA of
+    the convolution (4 per SM) runs at least two slabs -- the double-buffered halo, both tensor
+    memory accumulators and the mbarrier phase flips -- and every weight-gradient CTA loops over
+    several tiles."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = 64, 64, 48
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    mask = ((((x - 24) / 23) ** 2 + ((y - 32) / 31) ** 2 + ((z - 32) / 31) ** 2) < 1).astype(np.uint8)
+    mask[((x - 20) ** 2 + (y - 30) ** 2) < 36] = 0
+    rho = (1.0 + 0.01 * rng.normal(size=mask.shape)).astype(np.float32)
+    u = (0.03 * rng.normal(size=(3,) + mask.shape)).astype(np.float32)
+    ut = (u + 0.004 * rng.normal(size=u.shape)).astype(np.float32)
+    params = I.corrector_init_params(seed)
+    for k in (1, 3, 5):
+        params[k] = (0.05 * rng.normal(size=16)).astype(np.float32).astype(np.float64)
+    return mask, rho, u, ut, params
+
+
+def conv_work_counts(mask):
+    """(slabs, tiles) the library evaluates for a creation mask: 4^3 tiles holding fluid, dilated
+    by one tile, and the 8 x 16 x 1 slabs that meet them."""
+    nz, ny, nx = mask.shape
+    has = mask.reshape(nz // 4, 4, ny // 4, 4, nx // 4, 4).any(axis=(1, 3, 5))
+    p = np.pad(has, 1)
+    use = np.zeros_like(has)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                use |= p[dz:dz + has.shape[0], dy:dy + has.shape[1], dx:dx + has.shape[2]]
+    sl = use.reshape(use.shape[0], use.shape[1] // 4, 4, use.shape[2] // 2, 2).any(axis=(2, 4))
+    return 4 * int(sl.sum()), int(use.sum())
+
+
+def test_multi_slab_case_covers_every_cta_twice():
+    mask = _multi_slab_case()[0]
+    slabs, tiles = conv_work_counts(mask)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert slabs >= 2 * 4 * sms, (slabs, sms)
+    assert tiles >= 4 * 304
+
+
 def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
@@ -78,6 +121,38 @@ def test_gradients_match_oracle(seed):
         g, r = g.reshape(-1), r.reshape(-1)
         cos_min, rel_max = bounds[int(name[1])]
         cos = float(g @ r / (np.linalg.norm(g) * np.linalg.norm(r)))
+        assert cos >= cos_min, (name, cos)
+        assert _rel(g, r) <= rel_max, (name, _rel(g, r))
+
+
+def test_forward_matches_oracle_multi_slab():
+    """The forward pass where every convolution CTA walks two or more slabs."""
+    mask, rho, u, ut, params = _multi_slab_case(0)
+    net = lbm.Corrector(mask, params, US, RS, DS)
+    du = net.forward(_t(rho), _t(u)).cpu().numpy()
+    x0 = K.features(rho.astype(np.float64), u.astype(np.float64), mask, US, RS)
+    ref = K.correction(x0, mask, params, DS)
+    fl = mask > 0
+    assert _rel(du[:, fl], ref[:, fl]) < 2e-2
+    assert np.all(du[:, ~fl] == 0)
+
+
+def test_gradients_match_oracle_multi_slab():
+    """Loss and weight gradients where every convolution CTA (forward and data gradient) walks
+    two or more slabs and every weight-gradient CTA loops over several tiles."""
+    mask, rho, u, ut, params = _multi_slab_case(1)
+    net = lbm.Corrector(mask, params, US, RS, DS)
+    loss, grads = net.gradients(_t(rho), _t(u), _t(ut))
+    x0 = K.features(rho.astype(np.float64), u.astype(np.float64), mask, US, RS)
+    target = (ut.astype(np.float64) - u) / DS
+    ref_loss, ref_grads = K.loss_and_grad(x0, target, mask, params)
+    assert abs(loss - ref_loss) < 2e-2 * ref_loss
+    bounds = {1: (0.998, 8e-2), 2: (0.999, 5e-2), 3: (0.999, 3e-2)}
+    for name, g, r in zip(["W1", "b1", "W2", "b2", "W3", "b3"], grads, ref_grads):
+        g, r = g.reshape(-1), r.reshape(-1)
+        cos_min, rel_max = bounds[int(name[1])]
+        cos = float(g @ r / (np.linalg.norm(g) * np.linalg.norm(r)))
+        print(name, f"cos {cos:.6f} rel {_rel(g, r):.3e}")
         assert cos >= cos_min, (name, cos)
         assert _rel(g, r) <= rel_max, (name, _rel(g, r))
 

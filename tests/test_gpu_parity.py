@@ -28,18 +28,20 @@ oracle.set_threads(min(16, os.cpu_count() or 1))
 FP32_TOL = 1e-5
 
 
-def run_pair(g, steps, storage="fp32", init=None, ref_mask=None, scheme="esoteric", config=None):
+def run_pair(g, steps, storage="fp32", init=None, ref_mask=None, scheme="esoteric", config=None,
+             omega_hi=(1.0, 1.0, 1.0, 1.0), keep=False):
     """Advance the GPU domain and the oracle on geometry g; return both macroscopic fields.
     ref_mask: optional smaller z-slab for the oracle (translational invariance); config: a
-    launch configuration name (default: the library's)."""
-    dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme)
+    launch configuration name (default: the library's); omega_hi: the third- to sixth-order
+    rates of both sides; keep: also return the live domain and oracle case."""
+    dom = lbm.Domain.from_geometry(g, storage=storage, scheme=scheme, omega_hi=omega_hi)
     if config is not None:
         dom.set_launch_config(lbm.LAUNCH_CONFIG_NAMES.index(config))
     rm = g.mask if ref_mask is None else ref_mask
     links = g.links if ref_mask is None else None
     ref = oracle.Case(rm, periodic=g.periodic, links=links, inlet_center=g.inlet_center,
                       inlet_radius=g.inlet_radius, tau=g.tau, g0=g.g0, gamp=g.gamp, gomega=g.gomega,
-                      tau_cell=g.tau_cell if ref_mask is None else None)
+                      tau_cell=g.tau_cell if ref_mask is None else None, omega_hi=omega_hi)
     if g.wave is not None:
         ref.set_waveform(*g.wave)
     if init is not None:
@@ -51,8 +53,10 @@ def run_pair(g, steps, storage="fp32", init=None, ref_mask=None, scheme="esoteri
     rho, u = dom.macroscopic()
     rho_r, u_r = ref.macroscopic()
     info = dom.info()
-    dom.close()
     assert info["time"] == steps == ref.time
+    if keep:
+        return rho, u, rho_r, u_r, dom, ref
+    dom.close()
     return rho, u, rho_r, u_r
 
 
@@ -81,13 +85,94 @@ def test_taylor_green_init_equilibrium():
     assert np.abs(rho[0] - rho_r[0]).max() <= 1e-5
 
 
-@pytest.mark.parametrize("omega_hi", [(1.0, 1.0, 1.0, 1.0)])
-def test_bouzidi_pipe(omega_hi):
-    """Exact-q Bouzidi walls (both branches, tie-breaks) on a radius-9.3 pipe, 600 steps."""
+# third- to sixth-order rates, all different and away from 1, so that a swapped or mis-indexed
+# rate in the general collision path changes the flow by far more than the tolerance (measured on
+# the oracle: swapping any two of them moves max|u| by 1.2e-3 to 4.2e-3 relative on the pipe below
+# and 8.6e-3 to 3.6e-2 on the 64^3 aneurysm)
+GENERAL_RATES = (1.3, 0.9, 1.1, 1.7)
+
+
+@pytest.mark.parametrize("scheme", ["esoteric", "ab"])
+@pytest.mark.parametrize("omega_hi", [(1.0, 1.0, 1.0, 1.0), GENERAL_RATES])
+def test_bouzidi_pipe(omega_hi, scheme):
+    """Exact-q Bouzidi walls (both branches, tie-breaks) on a radius-9.3 pipe, 600 steps, with the
+    default rates (the second-order-only fast collision) and with general third- to fifth-order
+    rates (the general CHM-MRT path).  The pipe flow is z-invariant, so its sixth-order central
+    moment never leaves equilibrium (the oracle gives identical fields for any sixth-order
+    rate); the aneurysm test below pins that rate."""
     g = I.pipe(24, 24, 8, 9.3, center=(12.2, 11.9), tau=0.56, g0=(0.0, 0.0, 2e-6), bouzidi=True)
-    rho, u, rho_r, u_r = run_pair(g, 600)
+    rho, u, rho_r, u_r = run_pair(g, 600, scheme=scheme, omega_hi=omega_hi)
     assert rel_u(u, u_r) <= FP32_TOL
     assert np.abs(rho - rho_r).max() <= 1e-5
+
+
+@pytest.mark.parametrize("scheme", ["esoteric", "ab"])
+def test_synthetic_aneurysm_general_rates(scheme):
+    """The 64^3 synthetic aneurysm (Bouzidi walls, pulsatile inlet, outlet, absorbing layer) with
+    all four higher-order rates different from 1 and from each other, 400 steps, every cell.
+    The flow is fully three-dimensional, so every order reaches the result: on the oracle,
+    changing the sixth-order rate alone from 1.7 to 1.0 moves max|u| by 4e-3 relative, the
+    fifth-order rate from 1.1 to 1.0 by 1.4e-3."""
+    g = I.aneurysm(1, edge=64, period=400.0, reynolds=20.0)
+    rho, u, rho_r, u_r = run_pair(g, 400, scheme=scheme, omega_hi=GENERAL_RATES)
+    assert rel_u(u, u_r) <= FP32_TOL
+    assert np.abs(rho - rho_r).max() <= 1e-5
+
+
+def _open_face_normals(mask):
+    """Inward normal (axis, sign) of every inlet/outlet cell, from the box face it lies on."""
+    nz, ny, nx = mask.shape
+    zz, yy, xx = np.nonzero(mask >= 2)
+    axis = np.full(len(zz), -1)
+    sign = np.zeros(len(zz), int)
+    for ax, (pos, n) in enumerate(((xx, nx), (yy, ny), (zz, nz))):
+        lo, hi = pos == 0, pos == n - 1
+        axis[lo], sign[lo] = ax, 1
+        axis[hi], sign[hi] = ax, -1
+    assert np.all(axis >= 0)
+    return (zz, yy, xx), axis, sign
+
+
+def diagnostics_fp64(mask, rho, u):
+    """The FP64 sums lbm_get_diagnostics reports, written out over the dense fields: mass = sum
+    of rho over fluid cells, flux_in = sum over inlet cells of rho u.n_in, flux_out = sum over
+    outlet cells of -rho u.n_in, max_u = max |u| over fluid cells."""
+    rho = rho.astype(np.float64)
+    u = u.astype(np.float64)
+    fl = mask > 0
+    cells, axis, sign = _open_face_normals(mask)
+    un = u[axis, cells[0], cells[1], cells[2]] * sign
+    ru = rho[cells] * un
+    kind = mask[cells]
+    return {"mass": float(rho[fl].sum()), "flux_in": float(ru[kind == 2].sum()),
+            "flux_out": float(-ru[kind == 3].sum()), "max_u": float(np.sqrt((u[:, fl] ** 2).sum(axis=0)).max())}
+
+
+@pytest.mark.parametrize("case,scheme", [("inlet_pipe", "esoteric"), ("aneurysm", "esoteric"), ("aneurysm", "ab")])
+def test_diagnostics_match_oracle_sums(case, scheme):
+    """lbm_get_diagnostics (FP64 reductions on the device) against the same sums over the
+    oracle's FP64 fields: mass, inlet and outlet flow rates and max |u| within 1e-6 relative
+    (the fields themselves agree to the FP32 parity bar; the sums average the per-cell
+    differences).  Also against the sums over the GPU's own exported FP32 fields, where only the
+    summation order differs (1e-12): a wrong normal sign, a missing rho factor or a flux taken
+    over the wrong cells fails both."""
+    if case == "inlet_pipe":
+        g = I.inlet_pipe(32, 12, 12, 4.7, u_peak=0.02, tau=0.6)
+        g.wave = I.cardiac_waveform(3, period=300.0, u_peak=0.02)
+        steps = 600
+    else:
+        g = I.aneurysm(1, edge=64, period=400.0, reynolds=20.0)
+        steps = 400
+    rho, u, rho_r, u_r, dom, _ = run_pair(g, steps, scheme=scheme, keep=True)
+    d = dom.diagnostics()
+    dom.close()
+    own = diagnostics_fp64(g.mask, rho, u)
+    ref = diagnostics_fp64(g.mask, rho_r, u_r)
+    assert d["n_nonfinite"] == 0 and d["time"] == steps
+    assert ref["flux_in"] > 0 and ref["flux_out"] > 0
+    for key in ("mass", "flux_in", "flux_out", "max_u"):
+        assert abs(d[key] - own[key]) <= 1e-12 * abs(own[key]), (key, d[key], own[key])
+        assert abs(d[key] - ref[key]) <= 1e-6 * abs(ref[key]), (key, d[key], ref[key])
 
 
 def test_open_boundaries_pulsatile():
@@ -113,11 +198,15 @@ def test_synthetic_aneurysm_downscaled(seed, edge, scheme):
     assert np.abs(rho - rho_r).max() <= 1e-5
 
 
-def test_synthetic_aneurysm_full_size_short():
-    """The 256^3 synthetic aneurysm at Re 300 (tau ~ 0.506), Bouzidi walls, pulsatile inlet,
-    outlet: 30 steps in the benchmark's launch configuration, every fluid cell."""
+def test_synthetic_aneurysm_full_size_1000_steps():
+    """The 256^3 synthetic aneurysm at Re 300 (tau ~ 0.505), Bouzidi walls, pulsatile inlet,
+    outlet and absorbing layer: 1000 steps from rest (the inflow has crossed the inlet segment
+    and entered the bend), every fluid cell.  On the oracle alone, a 1e-7 relative perturbation
+    of every population moves max|u| by at most 5.3e-7 relative (step 100) and by 7.7e-8 at step
+    1000: at this resolution the flow damps rounding-size differences instead of amplifying
+    them, so the FP32 bar applies."""
     g = I.aneurysm(11, edge=256)
-    rho, u, rho_r, u_r = run_pair(g, 30)
+    rho, u, rho_r, u_r = run_pair(g, 1000)
     assert rel_u(u, u_r) <= FP32_TOL
     assert np.abs(rho - rho_r).max() <= 1e-5
 

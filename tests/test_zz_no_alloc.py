@@ -65,3 +65,21 @@ def test_noalloc_rejects_domains_beyond_its_scratch():
     assert "2097152" in lbm.load_library().lbm_last_error().decode()
     st, d = _via_abi(dom, "lbm_get_diagnostics")
     assert st == 0 and abs(d["mass"] - mask.size) < 1e-6
+
+
+def test_noalloc_at_exactly_its_limit():
+    """A fully fluid periodic 128^3 box has exactly 2,097,152 fluid cells, the largest domain the
+    fixed scratch serves: the reduction then uses every partial-sum block of the array and the
+    result record right after them.  Two calls in a row (the second after the flow has moved)
+    must match the allocating reduction."""
+    n = 128
+    mask = np.ones((n, n, n), np.uint8)
+    dom = lbm.Domain(mask, periodic=(1, 1, 1), tau=0.8, force=(1e-5, 0.0, 0.0))
+    assert dom.info()["n_fluid"] == 2_097_152
+    for _ in range(2):
+        dom.step(3)
+        st, got = _via_abi(dom, "lbm_get_diagnostics_noalloc")
+        st_ref, ref = _via_abi(dom, "lbm_get_diagnostics")
+        assert st == 0 and st_ref == 0
+        _assert_same(got, ref)
+        assert abs(got["mass"] - mask.size) < 1e-6 * mask.size and got["max_u"] > 0
