@@ -99,7 +99,7 @@ typedef void (*lbm_free_fn)(void* ptr, void* ctx);
 typedef struct {
     int32_t nx, ny, nz;
     int64_t n_fluid;         /* cells updated per step (mask 1, 2 or 3) */
-    int64_t n_bricks;        /* 4x4x4 bricks holding at least one fluid cell */
+    int64_t n_bricks;        /* 4x4x4 bricks holding at least one fluid or halo cell */
     int64_t n_slots;         /* 64 * n_bricks: population slots per direction */
     int64_t n_wall_cells;    /* fluid cells with at least one wall link */
     int64_t n_bouzidi_cells; /* fluid cells with at least one Bouzidi link */
@@ -111,6 +111,7 @@ typedef struct {
     int32_t launch_config;   /* launch configuration of the step kernel in use */
     int32_t scheme;          /* lbm_scheme */
     int64_t n_store_bricks;  /* bricks with population storage (active + twist halo) */
+    int64_t n_halo;          /* halo cells (mask value 4) of a sub-domain of a slab decomposition */
 } lbm_info;
 
 typedef struct {
@@ -128,9 +129,10 @@ void lbm_default_params(lbm_params* p);
 
 /*
  * Builds a domain from a voxel mask (Sec. 2.2: voxelised vessel geometry).
- *   mask[nx*ny*nz]: 0 solid, 1 fluid, 2 velocity inlet, 3 density outlet.  Inlet and outlet
- *     cells must lie on exactly one non-periodic box face; the face's inward normal is theirs.
- *     Neighbours outside a non-periodic face count as solid.
+ *   mask[nx*ny*nz]: 0 solid, 1 fluid, 2 velocity inlet, 3 density outlet, 4 halo (a cell of a
+ *     neighbouring sub-domain, see lbm_halo_pack).  Inlet and outlet cells must lie on exactly
+ *     one non-periodic box face; the face's inward normal is theirs.  Neighbours outside a
+ *     non-periodic face count as solid.
  *   Wall links (Sec. 2.1.4, q = |x_f - x_s| / |c|), n_links entries, may be 0 / NULL:
  *     link_cell[l]  box index of a cell with mask 1,
  *     link_dir[l]   direction beta with x_f + c_beta not fluid,
@@ -351,6 +353,38 @@ lbm_status lbm_mean_get(lbm_domain* dom, float* rho, float* u, int32_t dense, in
 lbm_status lbm_probe(lbm_domain* dom, const int64_t* fluid_index, int32_t n, float* out, int32_t device_ptrs);
 lbm_status lbm_similarity_index(const float* u_a, const float* u_b, const uint8_t* mask, int64_t n, double* si,
                                 void* cuda_stream);
+
+/*
+ * Slab decomposition: one domain split along one axis into sub-domains, each advanced by its own
+ * lbm_domain (several on one GPU, or one per GPU), with one exchange of face populations per
+ * step.  The method's cost is lattice points times steps (Sec. 3.4, Sec. 5: "per processor"),
+ * which the split shares out among processing units.
+ *   A sub-domain's mask marks the cells it receives from its neighbour with the value 4 (halo):
+ *   a one-cell layer on a non-periodic face of its box, holding the neighbour's layer of cells
+ *   next to the cut (4 where that cell is fluid, 0 where it is solid).  Halo cells need the A-B
+ *   scheme (INVALID_ARG otherwise) and must lie on a non-periodic face; they are stored but never
+ *   updated, they are not fluid cells (n_fluid, exports, diagnostics, means and probes leave them
+ *   out: lbm_info.n_halo counts them), and they count as fluid for their neighbours' wall links.
+ *   lbm_halo_size: *values = 9 x (area of the face) values per exchange buffer of `face`
+ *     (0 low x, 1 high x, 2 low y, 3 high y, 4 low z, 5 high z), 0 if that face has no halo
+ *     layer.  Positions on a face run over the other two axes, the lower axis fastest.
+ *   lbm_halo_pack: writes into buf[9][area] the populations of the current level's
+ *     post-collision state that leave the box through `face` (c . n_out = +1, in increasing
+ *     direction index) from the cells of the layer just inside the face's halo layer (0 where
+ *     that cell is not fluid).  buf is a device pointer; values keep the storage precision (4
+ *     bytes for FP32, 2 for FP16/BF16) and are copied bit for bit.
+ *   lbm_halo_unpack: writes buf, as packed by the neighbour on its face across the cut (the
+ *     same 9 directions, in the same order), into this face's halo layer, where the next
+ *     lbm_step pulls them.
+ *   Both enqueue on the domain's stream and return without waiting (buf must stay valid until
+ *   the work has run).  Exchanged after every lbm_step (and once after lbm_init_equilibrium or
+ *   lbm_apply_velocity_correction), the sub-domains reproduce the undivided domain's fields at
+ *   their fluid cells bit for bit.  Errors: INVALID_ARG (NULL, face outside 0..5, a face without
+ *   a halo layer), CUDA.
+ */
+lbm_status lbm_halo_size(const lbm_domain* dom, int32_t face, int64_t* values);
+lbm_status lbm_halo_pack(lbm_domain* dom, int32_t face, void* buf);
+lbm_status lbm_halo_unpack(lbm_domain* dom, int32_t face, const void* buf);
 
 /* Waits for all work enqueued on the domain. */
 lbm_status lbm_sync(lbm_domain* dom);

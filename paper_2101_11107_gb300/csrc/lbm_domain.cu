@@ -62,6 +62,12 @@ struct lbm_domain {
     std::vector<void*> owned;
     int64_t device_bytes = 0;
     float* d_corr_stage = nullptr;  // rho, u and a staged du for the velocity correction (lazy)
+    // halo layers (mask value 4, A-B only): per box face, the slots of the halo cells and of the
+    // fluid cells one layer inside, at every position of the face (-1: none)
+    int64_t n_halo = 0;
+    int32_t* d_halo_slot[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t* d_inner_slot[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t face_area[6] = {0, 0, 0, 0, 0, 0};
     // host copies kept for checkpoints
     uint64_t geometry_hash = 0;
 
@@ -234,10 +240,25 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     const int nbx = (nx + 3) / 4, nby = (ny + 3) / 4, nbz = (nz + 3) / 4;
     const int64_t n_brick_box = (int64_t)nbx * nby * nbz;
     std::vector<int32_t> brick_id((size_t)n_brick_box, -1);
-    int64_t n_fluid = 0;
+    int64_t n_fluid = 0, n_halo = 0;
     for (int64_t b = 0; b < n_box; ++b) {
-        if (mask[b] > 3) return fail(LBM_ERR_INVALID_ARG, "mask value > 3");
-        if (mask[b]) ++n_fluid;
+        if (mask[b] > 4) return fail(LBM_ERR_INVALID_ARG, "mask value > 4");
+        if (mask[b] == 4) ++n_halo;
+        else if (mask[b]) ++n_fluid;
+    }
+    // halo cells: stored, filled by lbm_halo_unpack, never updated; A-B only, on a box face
+    if (n_halo) {
+        if (P.scheme != LBM_SCHEME_AB) return fail(LBM_ERR_INVALID_ARG, "halo cells (mask 4) need the A-B scheme");
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    if (mask[x + (int64_t)nx * (y + (int64_t)ny * z)] != 4) continue;
+                    const int p[3] = {x, y, z};
+                    bool on_face = false;
+                    for (int d = 0; d < 3; ++d)
+                        if (!P.periodic[d] && (p[d] == 0 || p[d] == n3[d] - 1)) on_face = true;
+                    if (!on_face) return fail(LBM_ERR_INVALID_ARG, "a halo cell (mask 4) must lie on a non-periodic face");
+                }
     }
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -330,7 +351,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 const int64_t bi = x + (int64_t)nx * (y + (int64_t)ny * z);
-                if (!mask[bi]) continue;
+                if (!mask[bi] || mask[bi] == 4) continue;  // halo cells: word 0 (stored, not updated)
                 uint32_t w = WORD_FLUID;
                 if (tau_cell && tau_cell[bi] != P.tau) {
                     if (!(tau_cell[bi] > 0.5) || !std::isfinite(tau_cell[bi]))
@@ -433,6 +454,44 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     }
     const int64_t n_blinks = (int64_t)bq.size();
 
+    // ---------------------------------------------------------------- halo faces
+    // face f = 2 axis + side (side 1: the high face); positions of a face run over the other two
+    // axes, the lower one fastest.  halo_slot: the halo cell on the face; inner_slot: the fluid
+    // cell one layer inside.  Only faces that hold halo cells get tables.
+    std::vector<int32_t> halo_slot[6], inner_slot[6];
+    int64_t face_area[6] = {0, 0, 0, 0, 0, 0};
+    if (n_halo) {
+        for (int f = 0; f < 6; ++f) {
+            const int a = f / 2, side = f % 2;
+            const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+            const int64_t area = (int64_t)n3[b] * n3[c];
+            const int layer = side ? n3[a] - 1 : 0, inner = side ? n3[a] - 2 : 1;
+            std::vector<int32_t> hs((size_t)area, -1), is((size_t)area, -1);
+            bool any = false;
+            for (int v = 0; v < n3[c]; ++v)
+                for (int u = 0; u < n3[b]; ++u) {
+                    int p[3];
+                    p[a] = layer;
+                    p[b] = u;
+                    p[c] = v;
+                    const int64_t bi = p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2]);
+                    if (mask[bi] != 4) continue;
+                    any = true;
+                    hs[(size_t)(u + (int64_t)n3[b] * v)] = (int32_t)slot_of(p[0], p[1], p[2]);
+                    if (n3[a] < 2) continue;
+                    p[a] = inner;
+                    const int64_t ii = p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2]);
+                    if (mask[ii] >= 1 && mask[ii] <= 3)
+                        is[(size_t)(u + (int64_t)n3[b] * v)] = (int32_t)slot_of(p[0], p[1], p[2]);
+                }
+            if (any) {
+                halo_slot[f].swap(hs);
+                inner_slot[f].swap(is);
+                face_area[f] = area;
+            }
+        }
+    }
+
     // ---------------------------------------------------------------- device
     lbm_domain* D = new (std::nothrow) lbm_domain();
     if (!D) return fail(LBM_ERR_OOM, "host allocation failed");
@@ -479,6 +538,13 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     if (!st) st = upload(D, &d_io_sign, io_sign, "open-boundary sign");
     if (!st) st = upload(D, &D->d_fl_slot, fl_slot, "fluid slots");
     if (!st) st = upload(D, &D->d_fl_box, fl_box, "fluid box indices");
+    D->n_halo = n_halo;
+    for (int f = 0; f < 6 && !st; ++f) {
+        if (!face_area[f]) continue;
+        D->face_area[f] = face_area[f];
+        st = upload(D, &D->d_halo_slot[f], halo_slot[f], "halo slots");
+        if (!st) st = upload(D, &D->d_inner_slot[f], inner_slot[f], "halo inner slots");
+    }
     for (int k = 0; k < (twist ? 1 : 2) && !st; ++k) {
         D->d_pop[k] = D->dev_alloc(D->pop_bytes());
         if (!D->d_pop[k]) st = fail(LBM_ERR_OOM, "allocation failed: populations");
@@ -901,6 +967,7 @@ lbm_status lbm_get_info(const lbm_domain* D, lbm_info* out)
     I.launch_config = D->launch_config;
     I.scheme = D->params.scheme;
     I.n_store_bricks = D->n_store_bricks;
+    I.n_halo = D->n_halo;
     *out = I;
     return LBM_OK;
 }
@@ -1018,6 +1085,48 @@ lbm_status lbm_load_state(lbm_domain* D, const char* path)
         D->wave.clear();
     }
     return LBM_OK;
+}
+
+lbm_status lbm_halo_size(const lbm_domain* D, int32_t face, int64_t* values)
+{
+    g_last_error.clear();
+    if (!D || !values) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    if (face < 0 || face > 5) return fail(LBM_ERR_INVALID_ARG, "face must be 0..5");
+    *values = 9 * D->face_area[face];
+    return LBM_OK;
+}
+
+static lbm_status halo_copy(lbm_domain* D, int32_t face, void* buf, bool pack)
+{
+    g_last_error.clear();
+    if (!D || !buf) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
+    if (face < 0 || face > 5) return fail(LBM_ERR_INVALID_ARG, "face must be 0..5");
+    if (!D->face_area[face]) return fail(LBM_ERR_INVALID_ARG, "the face has no halo layer");
+    // pack: the populations leaving through the face (c . n_out = +1) from the layer inside the
+    // halo; unpack: the populations entering through it (c . n_out = -1) into the halo layer.
+    // Both list the directions with c_axis = (face high ? +1 : -1) for pack and the opposite for
+    // unpack, in increasing i -- the same list on the two sides of a cut.
+    const int a = face / 2, side = face % 2;
+    const int c_out = side ? +1 : -1;
+    const int want = pack ? c_out : -c_out;
+    HaloDirs dirs{};
+    int k = 0;
+    for (int i = 0; i < Q; ++i) {
+        const int ci = a == 0 ? cx_of(i) : a == 1 ? cy_of(i) : cz_of(i);
+        if (ci == want) dirs.d[k++] = (int8_t)i;
+    }
+    cudaError_t e = launch_halo_copy(D->bytes_per_value(), pack, D->src(), D->view.n_slots,
+                                     pack ? D->d_inner_slot[face] : D->d_halo_slot[face], D->face_area[face], dirs,
+                                     buf, D->stream);
+    if (e != cudaSuccess) return cuda_fail(e, pack ? "halo pack" : "halo unpack");
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_pack(lbm_domain* D, int32_t face, void* buf) { return halo_copy(D, face, buf, true); }
+
+lbm_status lbm_halo_unpack(lbm_domain* D, int32_t face, const void* buf)
+{
+    return halo_copy(D, face, const_cast<void*>(buf), false);
 }
 
 void lbm_destroy(lbm_domain* D)

@@ -132,6 +132,15 @@ const Launchers& launchers_fp16();
 const Launchers& launchers_bf16();
 const Launchers& launchers(int storage);
 
+// halo exchange of a slab decomposition: the 9 directions crossing a face, in increasing i
+struct HaloDirs {
+    int8_t d[9];
+};
+// pack: buf[j][p] = pop[dirs[j]][slot[p]] (0 where slot[p] < 0); unpack: the reverse where
+// slot[p] >= 0; values of bytes_per_value bytes, copied bit for bit
+cudaError_t launch_halo_copy(int bytes_per_value, bool pack, void* pop, int64_t n_slots, const int32_t* slot,
+                             int64_t area, const HaloDirs& dirs, void* buf, cudaStream_t stream);
+
 int64_t diagnostics_blocks(int64_t n_fluid);
 cudaError_t launch_diagnostics_final(const double* partials, int64_t n_blocks, lbm_diagnostics* out,
                                      cudaStream_t stream);

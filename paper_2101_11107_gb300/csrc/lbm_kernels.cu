@@ -47,6 +47,49 @@ __global__ void __launch_bounds__(dev::DIAG_THREADS)
 }
 }  // namespace
 
+namespace {
+// One thread per face position; every value is copied as raw bits (storage precision), so the
+// exchange is exact.
+template <typename T, bool PACK>
+__global__ void __launch_bounds__(256)
+    k_halo_copy(T* __restrict__ pop, uint32_t n_slots, const int32_t* __restrict__ slot, int64_t area, HaloDirs dirs,
+                T* __restrict__ buf)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= area) return;
+    const int32_t s = slot[p];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const uint32_t off = (uint32_t)dirs.d[j] * n_slots + (uint32_t)s;
+        if (PACK) buf[j * area + p] = s >= 0 ? pop[off] : T(0);
+        else if (s >= 0) pop[off] = buf[j * area + p];
+    }
+}
+}  // namespace
+
+cudaError_t launch_halo_copy(int bytes_per_value, bool pack, void* pop, int64_t n_slots, const int32_t* slot,
+                             int64_t area, const HaloDirs& dirs, void* buf, cudaStream_t stream)
+{
+    if (area == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((area + 255) / 256);
+    if (bytes_per_value == 4) {
+        if (pack)
+            k_halo_copy<uint32_t, true><<<grid, 256, 0, stream>>>(static_cast<uint32_t*>(pop), (uint32_t)n_slots, slot,
+                                                                 area, dirs, static_cast<uint32_t*>(buf));
+        else
+            k_halo_copy<uint32_t, false><<<grid, 256, 0, stream>>>(static_cast<uint32_t*>(pop), (uint32_t)n_slots, slot,
+                                                                  area, dirs, static_cast<uint32_t*>(buf));
+    } else {
+        if (pack)
+            k_halo_copy<uint16_t, true><<<grid, 256, 0, stream>>>(static_cast<uint16_t*>(pop), (uint32_t)n_slots, slot,
+                                                                 area, dirs, static_cast<uint16_t*>(buf));
+        else
+            k_halo_copy<uint16_t, false><<<grid, 256, 0, stream>>>(static_cast<uint16_t*>(pop), (uint32_t)n_slots, slot,
+                                                                  area, dirs, static_cast<uint16_t*>(buf));
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_diagnostics_final(const double* partials, int64_t n_blocks, lbm_diagnostics* out,
                                      cudaStream_t stream)
 {

@@ -27,7 +27,7 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_corrector_create", "lbm_corrector_get_params", "lbm_corrector_set_params", "lbm_corrector_forward",
            "lbm_corrector_gradients", "lbm_corrector_train_step", "lbm_corrector_apply", "lbm_corrector_destroy",
            "lbm_apply_velocity_correction", "lbm_restrict", "lbm_mean_reset", "lbm_mean_sample", "lbm_mean_get",
-           "lbm_probe", "lbm_similarity_index"]
+           "lbm_probe", "lbm_similarity_index", "lbm_halo_size", "lbm_halo_pack", "lbm_halo_unpack"]
 N_LAUNCH_CONFIGS = 8
 LAUNCH_CONFIG_NAMES = ["256x3", "128x7", "128x6", "128x8", "128x10", "pipe128x6", "2c128x4", "2c128x3"]
 SCHEME = {"ab": 0, "esoteric": 1}
@@ -55,7 +55,7 @@ class Info(ctypes.Structure):
                 ("n_open_cells", ctypes.c_int64), ("time", ctypes.c_int64), ("storage", ctypes.c_int32),
                 ("bytes_per_value", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("launch_config", ctypes.c_int32), ("scheme", ctypes.c_int32),
-                ("n_store_bricks", ctypes.c_int64)]
+                ("n_store_bricks", ctypes.c_int64), ("n_halo", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -127,6 +127,9 @@ def load_library(path: str = LIB_PATH):
     L.lbm_mean_get.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(i64)]
     L.lbm_probe.argtypes = [vp, vp, i32, vp, i32]
     L.lbm_similarity_index.argtypes = [vp, vp, vp, i64, ctypes.POINTER(dbl), vp]
+    L.lbm_halo_size.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.lbm_halo_pack.argtypes = [vp, i32, vp]
+    L.lbm_halo_unpack.argtypes = [vp, i32, vp]
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in ["lbm_create_domain", "lbm_set_inlet_waveform", "lbm_init_equilibrium", "lbm_step",
@@ -134,7 +137,8 @@ def load_library(path: str = LIB_PATH):
                  "lbm_save_state", "lbm_load_state", "lbm_set_launch_config", "lbm_autotune",
                  "lbm_get_diagnostics_noalloc", "lbm_batch_create", "lbm_batch_step",
                  "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_mean_reset", "lbm_mean_sample",
-                 "lbm_mean_get", "lbm_probe", "lbm_similarity_index"]:
+                 "lbm_mean_get", "lbm_probe", "lbm_similarity_index", "lbm_halo_size", "lbm_halo_pack",
+                 "lbm_halo_unpack"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -386,6 +390,21 @@ class Domain:
         else:
             a = np.ascontiguousarray(du, dtype=np.float32)
             _check(L.lbm_apply_velocity_correction(self._h, _ptr(a), 0))
+
+    # ---------------------------------------------------------------- slab decomposition
+    def halo_size(self, face):
+        """Values per exchange buffer of `face` (0 if it has no halo layer)."""
+        n = ctypes.c_int64()
+        _check(load_library().lbm_halo_size(self._h, int(face), ctypes.byref(n)))
+        return n.value
+
+    def halo_pack(self, face, buf):
+        """Post-collision populations leaving through `face` into the CUDA tensor buf (storage
+        precision: int32 for FP32, int16 for 16-bit storage, raw bits)."""
+        _check(load_library().lbm_halo_pack(self._h, int(face), ctypes.c_void_p(buf.data_ptr())))
+
+    def halo_unpack(self, face, buf):
+        _check(load_library().lbm_halo_unpack(self._h, int(face), ctypes.c_void_p(buf.data_ptr())))
 
     def save_state(self, path):
         _check(load_library().lbm_save_state(self._h, os.fsencode(path)))

@@ -71,7 +71,8 @@ def _create(L, mask, links=None, params=None, inlet_center=None, inlet_radius=0.
 @pytest.mark.parametrize("case", ["mask_value", "periodic_extent", "tau", "tau_nan", "omega", "link_not_wall",
                                   "link_q", "link_q_nan", "link_q_above_one", "link_rest_direction",
                                   "link_on_inlet", "duplicate_link", "open_cell_off_face",
-                                  "inlet_without_radius", "collision", "trt_magic"])
+                                  "inlet_without_radius", "collision", "trt_magic", "halo_twist",
+                                  "halo_inside", "halo_periodic_face", "link_into_halo"])
 def test_invalid_arguments_rejected_before_device_work(L, case):
     mask = np.ones((4, 8, 8), np.uint8)
     mask[:, :, 0] = 0
@@ -114,6 +115,18 @@ def test_invalid_arguments_rejected_before_device_work(L, case):
         kw["params"] = {"collision": 3}
     elif case == "trt_magic":
         kw["params"] = {"collision": 2, "trt_magic": -1.0}
+    elif case == "halo_twist":  # halo cells need the A-B scheme
+        mask[0, 2:6, 1:7] = 4
+    elif case == "halo_inside":  # a halo cell off every face
+        mask[2, 3, 3] = 4
+        kw["params"] = {"scheme": 0}
+    elif case == "halo_periodic_face":  # z wraps: z = 0 is no face
+        mask[0, 2:6, 1:7] = 4
+        kw["params"] = {"scheme": 0, "periodic": (0, 0, 1)}
+    elif case == "link_into_halo":  # a halo cell is fluid for its neighbours' links
+        mask[0, :, 1:7] = 4
+        kw["params"] = {"scheme": 0}
+        kw["links"] = ([2 + 8 * 3 + 64 * 1], [4], [0.4])  # -z neighbour of (2,3,1) is a halo cell
     if case == "link_on_inlet":
         pass
     st, msg, h = _create(L, mask, **kw)
