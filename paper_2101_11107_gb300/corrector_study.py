@@ -52,6 +52,85 @@ def geometry_pairs(seeds, fine_edge, period_f, reynolds, workers):
     return {s: (gf, gc) for s, gf, gc in out}
 
 
+def _geometry_at(args):
+    from . import inputs as I
+
+    seed, edge, period, reynolds = args
+    return seed, edge, I.aneurysm(seed, edge=edge, period=period, wave_seed=seed, reynolds=reynolds)
+
+
+def geometries_at_edges(seeds, edges, fine_edge, period_f, reynolds, workers):
+    """The same seeded aneurysms at other resolutions (acoustic scaling: the period in steps and
+    tau - 1/2 scale with the edge, the lattice velocity and Re stay); period_f * edge / fine_edge
+    must be an integer."""
+    jobs = []
+    for s in seeds:
+        for e in edges:
+            period = period_f * e / fine_edge
+            if period != int(period):
+                raise ValueError(f"edge {e}: the period {period} is not a whole number of steps")
+            jobs.append((s, e, int(period), reynolds))
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+        out = list(ex.map(_geometry_at, jobs))
+    return {(s, e): g for s, e, g in out}
+
+
+def sample_at_coarse_centres(u, mask, n_coarse):
+    """A velocity field u (3, e, e, e) on an e^3 grid sampled at the cell centres of the n_coarse^3
+    grid of the same box: trilinear interpolation over the fluid cells of `mask` (the weights of
+    non-fluid corners are dropped and the others renormalised), NaN where no corner is fluid.  For
+    e = 2 n_coarse every centre lies midway between 8 children with equal weights, so this is the
+    mean over the fluid children (the restriction of lbm_restrict); for e = n_coarse it is the
+    identity; in between, the one operator puts runs of every resolution on the coarse grid."""
+    e = mask.shape[0]
+    fl = (mask > 0).astype(np.float64)
+    idx, wts = [], []
+    for _ in range(3):
+        xc = (np.arange(n_coarse) + 0.5) * e / n_coarse - 0.5
+        i0 = np.floor(xc).astype(np.int64)
+        f = xc - i0
+        i1 = np.minimum(i0 + 1, e - 1)
+        idx.append((i0, i1))
+        wts.append((1.0 - f, f))
+    num = np.zeros((3, n_coarse, n_coarse, n_coarse))
+    den = np.zeros((n_coarse, n_coarse, n_coarse))
+    for bz in (0, 1):
+        for by in (0, 1):
+            for bx in (0, 1):
+                zi, yi, xi = idx[2][bz], idx[1][by], idx[0][bx]
+                w = wts[2][bz][:, None, None] * wts[1][by][None, :, None] * wts[0][bx][None, None, :]
+                w = w * fl[np.ix_(zi, yi, xi)]
+                den += w
+                num += w[None] * u[(slice(None),) + np.ix_(zi, yi, xi)]
+    out = np.full_like(num, np.nan)
+    ok = den > 0
+    out[:, ok] = num[:, ok] / den[ok]
+    return out
+
+
+def rel_error_on_coarse(u_run, u_fine, coarse_mask):
+    """Relative L2 error of u_run against u_fine (both sampled on the coarse grid) over the
+    coarse fluid cells where both are defined."""
+    ok = (coarse_mask > 0) & np.all(np.isfinite(u_run), axis=0) & np.all(np.isfinite(u_fine), axis=0)
+    return float(np.linalg.norm((u_run - u_fine)[:, ok]) / np.linalg.norm(u_fine[:, ok]))
+
+
+def equal_error_point(edges, errors, walls, target):
+    """The resolution at which the plain solver's error (decreasing with the edge) reaches
+    `target`, by linear interpolation of the error in the edge between the two bracketing
+    resolutions, and its wall time, by interpolation of log(wall) in log(edge).  None if the
+    target lies outside the resolutions run."""
+    pts = sorted(zip(edges, errors, walls))
+    for (e0, r0, w0), (e1, r1, w1) in zip(pts[:-1], pts[1:]):
+        if (r0 - target) * (r1 - target) <= 0 and r0 != r1:
+            t = (r0 - target) / (r0 - r1)
+            e = e0 + t * (e1 - e0)
+            lw = np.log(w0) + (np.log(e) - np.log(e0)) / (np.log(e1) - np.log(e0)) * (np.log(w1) - np.log(w0))
+            return {"edge": float(e), "wall_s": float(np.exp(lw)), "between": [e0, e1]}
+    return None
+
+
 def correct_or_fall_back(coarse, corrector, mask, out_mask, gain):
     """One in-loop correction of a running coarse domain, with the plain solver as fallback:
     the corrector nudges the domain's state; if the corrected state has a non-finite cell (FP64
@@ -75,7 +154,7 @@ def similarity_index(u_hr, u_lr, mask):
 
 
 def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples_per_period, train_steps, lr,
-        apply_every, workers, log, gain=0.25, dagger_rounds=0, dagger_steps=None):
+        apply_every, workers, log, gain=0.25, dagger_rounds=0, dagger_steps=None, compare_edges=()):
     import torch
 
     from . import inputs as I
@@ -83,7 +162,9 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
 
     t0 = time.time()
     pairs = geometry_pairs(list(train_seeds) + list(test_seeds), fine_edge, period_f, reynolds, workers)
-    log(f"geometries: {len(pairs)} pairs in {time.time() - t0:.1f} s")
+    extra = geometries_at_edges(test_seeds, compare_edges, fine_edge, period_f, reynolds, workers) \
+        if compare_edges else {}
+    log(f"geometries: {len(pairs)} pairs and {len(extra)} at other resolutions in {time.time() - t0:.1f} s")
     torch.cuda.set_device(0)
     period_c = period_f // 2
     n_c = periods * period_c
@@ -291,13 +372,50 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
             torch.cuda.synchronize()
             times[name] = ev0.elapsed_time(ev1) / 1e3
             b.close()
+        # plain runs at intermediate resolutions, sampled on the coarse grid at the same physical
+        # times, and timed like the others (for the comparison at equal error)
+        plain_at = {}
+        n_coarse = cm.shape[0]
+        for e in compare_edges:
+            ge = extra[(s, e)]
+            errs = []
+            dom = lbm.Domain.from_geometry(ge)
+            for a in plain:
+                te = a["t"] * e / n_coarse
+                if te != int(te):
+                    raise ValueError(f"edge {e}: sample time {te} is not a whole step")
+                dom.step(int(te) - dom.time)
+                ue = dom.macroscopic()[1].astype(np.float64)
+                us = sample_at_coarse_centres(ue, ge.mask, n_coarse)
+                errs.append(rel_error_on_coarse(us, a["u_fine"].cpu().numpy().astype(np.float64), cm))
+            dom.close()
+            steps_e = n_c * e // n_coarse
+            dom = lbm.Domain.from_geometry(ge)
+            b = lbm.Batch([dom], graph_steps=apply_every)
+            b.step(apply_every)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            b.step(steps_e)
+            ev1.record()
+            torch.cuda.synchronize()
+            plain_at[int(e)] = {"err": float(np.mean(errs)), "wall_s": ev0.elapsed_time(ev1) / 1e3,
+                                "fluid": int(ge.nfluid), "steps": int(steps_e)}
+            b.close()
+            dom.close()
+        # the plain coarse run through the same sampling operator (the identity at n_coarse)
+        e_plain_resampled = []
+        for a in plain:
+            us = sample_at_coarse_centres(a["u"].cpu().numpy().astype(np.float64), cm, n_coarse)
+            e_plain_resampled.append(rel_error_on_coarse(us, a["u_fine"].cpu().numpy().astype(np.float64), cm))
         r = {"seed": int(s), "fine_fluid": int(gf.nfluid), "coarse_fluid": int(gc.nfluid), "tau_fine": gf.tau,
              "tau_coarse": gc.tau, "err_plain": float(np.mean(e_plain)), "err_corrected": float(np.mean(e_corr)),
              "err_output_corrected": float(np.mean(e_out)),
+             "err_plain_resampled": float(np.mean(e_plain_resampled)),
              "si_plain": float(np.mean(si_plain)), "si_corrected": float(np.mean(si_corr)),
              "si_output_corrected": float(np.mean(si_out)),
              "fallback_at_step": corr[0].get("fallback") if corr else None,
-             "wall_s": times}
+             "wall_s": times, "plain_at_edge": plain_at}
         log(json.dumps(r))
         results.append(r)
     summary = {
@@ -317,6 +435,24 @@ def run(fine_edge, period_f, reynolds, train_seeds, test_seeds, periods, samples
         "wall_coarse_corrector_s": float(np.mean([r["wall_s"]["coarse+corrector"] for r in results])),
         "per_geometry": results,
     }
+    if compare_edges:
+        # mean error and wall time of the plain solver against resolution (the coarse grid, the
+        # intermediate grids, and the fine grid, whose error against itself is 0), and the
+        # resolution and wall time at which it matches coarse + corrector's error
+        edges = [fine_edge // 2] + [int(e) for e in compare_edges] + [fine_edge]
+        errs = [summary["err_plain_mean"]] + \
+            [float(np.mean([r["plain_at_edge"][int(e)]["err"] for r in results])) for e in compare_edges] + [0.0]
+        walls = [summary["wall_coarse_s"]] + \
+            [float(np.mean([r["plain_at_edge"][int(e)]["wall_s"] for r in results])) for e in compare_edges] + \
+            [summary["wall_fine_s"]]
+        pt = equal_error_point(edges, errs, walls, summary["err_corrected_mean"])
+        summary["equal_error"] = {
+            "edges": edges, "err_plain_by_edge": errs, "wall_plain_by_edge_s": walls,
+            "target_err": summary["err_corrected_mean"], "plain_at_equal_error": pt,
+            "wall_coarse_corrector_s": summary["wall_coarse_corrector_s"],
+            "speedup_vs_plain_at_equal_error": (pt["wall_s"] / summary["wall_coarse_corrector_s"]) if pt else None,
+            "speedup_vs_fine": summary["wall_fine_s"] / summary["wall_coarse_corrector_s"],
+            "err_plain_resampled_mean": float(np.mean([r["err_plain_resampled"] for r in results]))}
     return summary, net
 
 
@@ -329,6 +465,8 @@ def main(argv=None):
     ap.add_argument("--dagger", type=int, default=None,
                     help="rounds of in-loop data collection and training (default 4; --small: 2)")
     ap.add_argument("--gain", type=float, default=0.25)
+    ap.add_argument("--compare-edges", default="",
+                    help="comma-separated intermediate resolutions run plain for the comparison at equal error")
     a = ap.parse_args(argv)
     if a.small:
         cfg = dict(fine_edge=128, period_f=800, reynolds=60.0, train_seeds=list(range(100, 116)),
@@ -338,8 +476,9 @@ def main(argv=None):
                    test_seeds=list(range(200, 208)), periods=3, samples_per_period=10, train_steps=4000, lr=1e-3,
                    apply_every=50)
     dagger = a.dagger if a.dagger is not None else (2 if a.small else 4)
+    edges = tuple(int(e) for e in a.compare_edges.split(",") if e)
     summary, net = run(workers=a.workers, log=lambda m: print(m, flush=True), dagger_rounds=dagger, gain=a.gain,
-                       **cfg)
+                       compare_edges=edges, **cfg)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(summary, f, indent=1)
