@@ -664,6 +664,7 @@ lbm_status lbm_init_equilibrium(lbm_domain* D, const float* rho, const float* u,
 
 lbm_status lbm_step(lbm_domain* D, int64_t n)
 {
+    NvtxRange nvtx_range("lbm_step");
     g_last_error.clear();
     if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
     if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
@@ -699,6 +700,7 @@ static bool config_applies(const lbm_domain* D, int c)
 
 lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config, float* ms_per_step)
 {
+    NvtxRange nvtx_range("lbm_autotune");
     g_last_error.clear();
     if (!D || trial_steps < 1) return fail(LBM_ERR_INVALID_ARG, "bad arguments");
     if (D->n_bricks == 0) {
@@ -762,6 +764,7 @@ lbm_status lbm_autotune(lbm_domain* D, int32_t trial_steps, int32_t* best_config
 
 lbm_status lbm_get_macroscopic(lbm_domain* D, float* rho, float* u, int32_t dense, int32_t device_ptrs)
 {
+    NvtxRange nvtx_range("lbm_get_macroscopic");
     g_last_error.clear();
     if (!D || !rho || !u) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
     const int64_t n_out = dense ? (int64_t)D->nx * D->ny * D->nz : D->n_fluid;
@@ -893,6 +896,7 @@ lbm_status lbm_probe(lbm_domain* D, const int64_t* fluid_index, int32_t n, float
 
 lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t device_ptrs)
 {
+    NvtxRange nvtx_range("lbm_apply_velocity_correction");
     g_last_error.clear();
     if (!D || !du) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
     const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
@@ -929,6 +933,7 @@ lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t
 
 lbm_status lbm_get_diagnostics(lbm_domain* D, lbm_diagnostics* out)
 {
+    NvtxRange nvtx_range("lbm_get_diagnostics");
     g_last_error.clear();
     if (!D || !out) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
     const LevelArgs a = D->level_args(D->time);
@@ -1098,6 +1103,7 @@ lbm_status lbm_halo_size(const lbm_domain* D, int32_t face, int64_t* values)
 
 static lbm_status halo_copy(lbm_domain* D, int32_t face, void* buf, bool pack)
 {
+    NvtxRange nvtx_range("lbm_halo_copy");
     g_last_error.clear();
     if (!D || !buf) return fail(LBM_ERR_INVALID_ARG, "NULL argument");
     if (face < 0 || face > 5) return fail(LBM_ERR_INVALID_ARG, "face must be 0..5");
@@ -1307,6 +1313,7 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
 
 lbm_status lbm_batch_step(lbm_batch* B, int64_t n)
 {
+    NvtxRange nvtx_range("lbm_batch_step");
     g_last_error.clear();
     if (!B) return fail(LBM_ERR_INVALID_ARG, "NULL batch");
     if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");

@@ -3,11 +3,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/lbm.h"
 
 namespace lbm {
+
+// An NVTX range over a scope: entry points that enqueue or run device work mark themselves on
+// the host timeline of a profiler (nvtx3 is header-only; without a tool attached a push/pop is
+// a test of a null function pointer).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // D3Q27, i = (cx+1) + 3 (cy+1) + 9 (cz+1); opposite = 26 - i.  Weights are the products of the
 // D1Q3 weights (2/3, 1/6, 1/6): 8/27, 2/27, 1/54, 1/216 by |c|^2.

@@ -837,6 +837,7 @@ lbm_status lbm_corrector_set_params(lbm_corrector* K, const float* params)
 lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
                                  const float* u, float* du)
 {
+    NvtxRange nvtx_range("lbm_corrector_forward");
     if (!K || !rho || !u || !du) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = K->forward(mask, rho, u);
     const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
@@ -853,6 +854,7 @@ lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const ui
 lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
                                    const float* u, const float* u_target, float* grad, double* loss)
 {
+    NvtxRange nvtx_range("lbm_corrector_gradients");
     if (!K || !rho || !u || !u_target || !grad || !loss) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = K->forward(mask, rho, u);
     if (e == cudaSuccess) e = K->backward(out_mask ? out_mask : (mask ? mask : K->mask), u, u_target);
@@ -871,6 +873,7 @@ lbm_status lbm_corrector_gradients(lbm_corrector* K, const uint8_t* mask, const 
 lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const uint8_t* out_mask, const float* rho,
                                     const float* u, const float* u_target, double lr, double* loss)
 {
+    NvtxRange nvtx_range("lbm_corrector_train_step");
     if (!K || !rho || !u || !u_target) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     if (!(lr > 0.0)) return nn_fail(LBM_ERR_INVALID_ARG, "lr must be > 0");
     cudaError_t e = K->forward(mask, rho, u);
@@ -899,6 +902,7 @@ lbm_status lbm_corrector_train_step(lbm_corrector* K, const uint8_t* mask, const
 lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t* mask, const uint8_t* out_mask,
                                double gain)
 {
+    NvtxRange nvtx_range("lbm_corrector_apply");
     if (!K || !dom) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     if (!(gain > 0.0 && gain <= 1.0)) return nn_fail(LBM_ERR_INVALID_ARG, "gain must lie in (0, 1]");
     lbm_info I{};
@@ -942,6 +946,7 @@ void lbm_corrector_destroy(lbm_corrector* K)
 lbm_status lbm_restrict(const float* fine_rho, const float* fine_u, const uint8_t* fine_mask, int32_t fnx, int32_t fny,
                         int32_t fnz, float* coarse_rho, float* coarse_u, void* cuda_stream)
 {
+    NvtxRange nvtx_range("lbm_restrict");
     if (!fine_rho || !fine_u || !fine_mask || !coarse_rho || !coarse_u) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
     if (fnx <= 0 || fny <= 0 || fnz <= 0 || fnx % 2 || fny % 2 || fnz % 2)
         return nn_fail(LBM_ERR_INVALID_ARG, "fine extents must be positive and even");

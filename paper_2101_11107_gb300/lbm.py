@@ -210,6 +210,8 @@ class Domain:
         p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
         p.trt_magic = trt_magic
         self.storage = storage
+        self.collision = collision
+        self.omega_hi = tuple(float(w) for w in omega_hi)
         if links is None or len(links[0]) == 0:
             lc = ld = lq = None
             n_links = 0
@@ -351,13 +353,28 @@ class Domain:
     def set_launch_config(self, config):
         _check(load_library().lbm_set_launch_config(self._h, int(config)))
 
-    def autotune(self, trial_steps=20):
+    def autotune(self, trial_steps=20, cache=None):
         """Times every launch configuration on this domain and keeps the fastest; returns
-        (best, {name: ms_per_step})."""
+        (best, {name: ms_per_step}).  cache: path of a JSON file of earlier choices keyed by GPU
+        and domain configuration (autotune_cache_key); a hit selects the stored configuration
+        without timing (self.autotuned_from_cache tells which happened), a miss times and adds
+        the result."""
+        key = autotune_cache_key(self) if cache else None
+        if key is not None:
+            hit = autotune_cache_get(cache, key)
+            if hit is not None:
+                self.set_launch_config(LAUNCH_CONFIG_NAMES.index(hit["best"]))
+                self.autotuned_from_cache = True
+                return LAUNCH_CONFIG_NAMES.index(hit["best"]), dict(hit["ms"])
         best = ctypes.c_int32()
         ms = (ctypes.c_float * N_LAUNCH_CONFIGS)()
         _check(load_library().lbm_autotune(self._h, int(trial_steps), ctypes.byref(best), ms))
-        return best.value, dict(zip(LAUNCH_CONFIG_NAMES, list(ms)))
+        out = dict(zip(LAUNCH_CONFIG_NAMES, [float(v) for v in ms]))
+        self.autotuned_from_cache = False
+        if key is not None:
+            autotune_cache_put(cache, key, {"best": LAUNCH_CONFIG_NAMES[best.value], "ms": out,
+                                            "trial_steps": int(trial_steps)})
+        return best.value, out
 
     def diagnostics_noalloc(self, raise_unstable=True) -> dict:
         """lbm_get_diagnostics_noalloc: the same reduction with the library's fixed scratch
@@ -411,6 +428,55 @@ class Domain:
 
     def load_state(self, path):
         _check(load_library().lbm_load_state(self._h, os.fsencode(path)))
+
+
+def autotune_cache_key(dom) -> str:
+    """Key of a domain's autotuning result: the GPU (name, SM count, compute capability), the
+    library file (size and modification time: a rebuilt library is tuned again), and what the
+    step kernel's speed depends on -- storage, scheme, collision operator and whether the
+    higher-order rates are all 1 (the second-order-only collision), box extents, fluid cells,
+    bricks and wall / Bouzidi / open cells."""
+    import json
+
+    import torch
+    pr = torch.cuda.get_device_properties(dom.device)
+    st = os.stat(LIB_PATH)
+    i = dom.info()
+    return json.dumps({"gpu": pr.name, "sms": pr.multi_processor_count, "cc": [pr.major, pr.minor],
+                       "lib": [st.st_size, int(st.st_mtime)], "storage": i["storage"], "scheme": i["scheme"],
+                       "collision": str(dom.collision), "unit_rates": all(w == 1.0 for w in dom.omega_hi),
+                       "box": [i["nx"], i["ny"], i["nz"]], "fluid": i["n_fluid"], "bricks": i["n_bricks"],
+                       "wall": i["n_wall_cells"], "bouzidi": i["n_bouzidi_cells"], "open": i["n_open_cells"]},
+                      sort_keys=True)
+
+
+def autotune_cache_get(path, key):
+    """The stored entry for key in the JSON cache file at path, or None (no file, no entry, or an
+    unreadable file)."""
+    import json
+
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def autotune_cache_put(path, key, value):
+    """Adds or replaces key in the JSON cache file (written to a temporary file and renamed, so
+    that a reader never sees a partial file)."""
+    import json
+
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[key] = value
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def similarity_index(u_a, u_b, mask=None, stream=None) -> float:

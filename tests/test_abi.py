@@ -185,3 +185,22 @@ def test_batch_corrector_and_restriction_reject_invalid_arguments(L):
     assert L.lbm_restrict(lbm._ptr(buf), lbm._ptr(buf), lbm._ptr(fm), 3, 4, 4, lbm._ptr(buf), lbm._ptr(buf),
                           None) == 1
     assert L.lbm_restrict(None, lbm._ptr(buf), lbm._ptr(fm), 4, 4, 4, lbm._ptr(buf), lbm._ptr(buf), None) == 1
+
+
+def test_autotune_cache_file(tmp_path):
+    """The autotuner's JSON cache: a miss returns None (also for a missing or corrupt file), a
+    stored entry comes back, a second key leaves the first in place, and the file is valid JSON
+    after every write."""
+    import json
+
+    path = str(tmp_path / "tune.json")
+    assert lbm.autotune_cache_get(path, "k1") is None
+    lbm.autotune_cache_put(path, "k1", {"best": "128x6", "ms": {"128x6": 0.03}})
+    assert lbm.autotune_cache_get(path, "k1")["best"] == "128x6"
+    lbm.autotune_cache_put(path, "k2", {"best": "2c128x4", "ms": {}})
+    data = json.load(open(path))
+    assert set(data) == {"k1", "k2"} and data["k2"]["best"] == "2c128x4"
+    open(path, "w").write("{not json")
+    assert lbm.autotune_cache_get(path, "k1") is None
+    lbm.autotune_cache_put(path, "k3", {"best": "128x7", "ms": {}})
+    assert set(json.load(open(path))) == {"k3"}

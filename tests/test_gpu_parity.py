@@ -495,3 +495,20 @@ def test_maximum_size_box_z_invariant():
     rr, ur = ref.macroscopic()
     assert rel_u(u0g, ur) <= FP32_TOL
     assert np.abs(r0 - rr).max() <= 1e-5
+
+
+def test_autotune_cache_hit_skips_timing(tmp_path):
+    """A second domain of the same configuration takes the cached launch configuration without
+    timing; a different storage precision is a miss."""
+    path = str(tmp_path / "tune.json")
+    g = I.aneurysm(4, edge=64, period=200.0)
+    a = lbm.Domain.from_geometry(g)
+    best, ms = a.autotune(5, cache=path)
+    assert a.autotuned_from_cache is False
+    b = lbm.Domain.from_geometry(g)
+    best_b, ms_b = b.autotune(5, cache=path)
+    assert b.autotuned_from_cache is True and best_b == best and ms_b == ms
+    assert b.info()["launch_config"] == best
+    c = lbm.Domain.from_geometry(g, storage="fp16")
+    c.autotune(5, cache=path)
+    assert c.autotuned_from_cache is False
