@@ -45,6 +45,26 @@ namespace dev {
 
 constexpr float CS2 = 1.0f / 3.0f;
 
+// ------------------------------------------------------------------------------ LBM_DEBUG
+// Built with -DLBM_DEBUG, every access of a population array, the Bouzidi q and side lists and
+// the open-boundary records is checked against the array's extent first: an access out of range
+// is skipped (a load gives 0) and the check's code is kept in a device flag of this translation
+// unit (the first one wins), which the host reads at its next synchronising call.  Codes:
+// 1 A-B pull, 2 twist load, 3 twist store, 4 A-B store, 5 Bouzidi q / side list, 6 open-boundary
+// record, 7 velocity-correction update.  Without the macro every check is the constant true.
+#ifdef LBM_DEBUG
+static __device__ unsigned int g_debug_fault = 0u;
+__device__ __forceinline__ bool dbg_in_range(uint64_t i, uint64_t n, unsigned code)
+{
+    if (i < n) return true;
+    atomicCAS(&g_debug_fault, 0u, code);
+    return false;
+}
+#define LBM_IN_RANGE(i, n, code) ::lbm::dev::dbg_in_range((uint64_t)(i), (uint64_t)(n), (code))
+#else
+#define LBM_IN_RANGE(i, n, code) true
+#endif
+
 // ------------------------------------------------------------------------------ storage
 // FP32 stores d_i; FP16 / BF16 store d_i / w_i.  `load` may use the read-only path (arrays
 // not written by the kernel); `load_rw` is a plain load (the in-place array).
@@ -142,7 +162,7 @@ __device__ __forceinline__ void fetch_ab(const void* __restrict__ src, uint32_t 
         const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
-        d[i] = Store<ST>::load(src, i, off);
+        d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load(src, i, off) : 0.0f;
     }
 }
 
@@ -163,7 +183,7 @@ __device__ __forceinline__ void fetch_ab_shfl(const void* __restrict__ src, uint
         const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
-        if (fluid) d[i] = Store<ST>::load(src, i, off);
+        if (fluid) d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load(src, i, off) : 0.0f;
     }
 }
 
@@ -206,7 +226,8 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint32_t off = (PC ? (uint32_t)(Q - 1 - i) : (uint32_t)i) * n + cs[corner_neg(i)];
-            d[i] = RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off);
+            d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off))
+                                                        : 0.0f;
         }
         return;
     }
@@ -216,7 +237,8 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
         const uint32_t flip = ((uint32_t)parity ^ (wm >> i)) & 1u;
         const uint32_t dir = flip ? (uint32_t)(Q - 1 - i) : (uint32_t)i;
         const uint32_t off = dir * n + cs[corner_neg(i)];
-        d[i] = RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off);
+        d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off))
+                                                    : 0.0f;
     }
 }
 
@@ -236,8 +258,10 @@ __device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const uint32_t dir = parity ? (uint32_t)i : (uint32_t)(Q - 1 - i);
-        if (X) Store<ST>::store_x(pop, i, dir * n + cs[corner_pos(i)], d[i]);
-        else Store<ST>::store(pop, i, dir * n + cs[corner_pos(i)], d[i]);
+        const uint32_t off = dir * n + cs[corner_pos(i)];
+        if (!LBM_IN_RANGE(off, (uint64_t)Q * n, 3)) continue;
+        if (X) Store<ST>::store_x(pop, i, off, d[i]);
+        else Store<ST>::store(pop, i, off, d[i]);
     }
 }
 
@@ -325,6 +349,7 @@ __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* 
         for (int i = 0; i < Q; ++i) {
             if (!(wm & (1u << i))) continue;
             const uint32_t li = link_index(off, wm, i);
+            if (!LBM_IN_RANGE(li, v.n_bq, 5)) continue;
             const float q = __ldg(v.bq + li);
             // loaded whatever q is, so that the two loads do not wait on each other
             const float fa = (SCHEME == LBM_SCHEME_ESOTERIC)
@@ -342,7 +367,8 @@ __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* 
         }
     } else if (kind >= KIND_INLET) {
         const int64_t rec = v.aux[slot];
-        close_open(d, kind, v.io_axis[rec], v.io_sign[rec], v.io_phi[rec], a.U, a.rho_out, a.drho_out);
+        if (LBM_IN_RANGE(rec, v.n_io, 6))
+            close_open(d, kind, v.io_axis[rec], v.io_sign[rec], v.io_phi[rec], a.U, a.rho_out, a.drho_out);
     }
     return half;
 }
@@ -737,7 +763,7 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
             const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if (half & (1u << i)) {
+                if ((half & (1u << i)) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5)) {
                     if (X) Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
                     else Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
                 }
@@ -750,6 +776,7 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         collide_model<COLL, X>(d, la);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
+            if (!LBM_IN_RANGE((uint32_t)i * n + slot, (uint64_t)Q * n, 4)) continue;
             if (X) Store<ST>::store_x(dst, i, (uint32_t)i * n + slot, d[i]);
             else Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
         }
@@ -781,7 +808,8 @@ __device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop,
         const uint32_t wm = __ldg(v.word + slot) & WORD_WALL_MASK;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            if (half & (1u << i)) Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
+            if ((half & (1u << i)) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5))
+                Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
     }
 }
 
@@ -865,7 +893,8 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
                 for (int i = 0; i < Q; ++i) {
                     const uint32_t flip = ((uint32_t)a.parity ^ (wm >> i)) & 1u;
                     const uint32_t dir = flip ? (uint32_t)(Q - 1 - i) : (uint32_t)i;
-                    cp_async4(&stage[(st * Q + i) * T + tid], pop + dir * n + cs[corner_neg(i)]);
+                    if (LBM_IN_RANGE(dir * n + cs[corner_neg(i)], (uint64_t)Q * n, 2))
+                        cp_async4(&stage[(st * Q + i) * T + tid], pop + dir * n + cs[corner_neg(i)]);
                 }
             }
         }
@@ -897,7 +926,8 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
                     const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (half & (1u << i)) Store<LBM_STORE_FP32>::store(v.side, i, link_index(off, wm, i), d[i]);
+                        if ((half & (1u << i)) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5))
+                            Store<LBM_STORE_FP32>::store(v.side, i, link_index(off, wm, i), d[i]);
                 }
             }
         }
@@ -1037,11 +1067,13 @@ __global__ void __launch_bounds__(256)
             const uint32_t wm = word & WORD_WALL_MASK;
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if ((wm >> i) & 1u) Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
+                if (((wm >> i) & 1u) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5))
+                    Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
+        for (int i = 0; i < Q; ++i)
+            if (LBM_IN_RANGE((uint32_t)i * n + slot, (uint64_t)Q * n, 4)) Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
     }
 }
 
@@ -1090,7 +1122,7 @@ __global__ void __launch_bounds__(256)
         for (int i = 0; i < Q; ++i) {
             const uint32_t dir = parity_prev ? (uint32_t)i : (uint32_t)(Q - 1 - i);
             const uint32_t off = dir * n + cs[corner_pos(i)];
-            Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
+            if (LBM_IN_RANGE(off, (uint64_t)Q * n, 7)) Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
         }
         const uint32_t word = v.word[slot];
         if (((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) {
@@ -1098,7 +1130,7 @@ __global__ void __launch_bounds__(256)
             const uint32_t wm = word & WORD_WALL_MASK;
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if ((wm >> i) & 1u) {
+                if (((wm >> i) & 1u) && LBM_IN_RANGE(link_index(off0, wm, i), v.n_bq, 5)) {
                     const uint32_t off = link_index(off0, wm, i);
                     Store<ST>::store(v.side, i, off, Store<ST>::load_rw(v.side, i, off) + delta[i]);
                 }
@@ -1107,7 +1139,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint32_t off = (uint32_t)i * n + slot;
-            Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
+            if (LBM_IN_RANGE(off, (uint64_t)Q * n, 7)) Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
         }
     }
 }
@@ -1156,7 +1188,7 @@ __global__ void __launch_bounds__(DIAG_THREADS)
         if (finite) {
             x[0] = (double)M.rho;
             const int kind = (int)((word >> WORD_KIND_SHIFT) & 3u);
-            if (kind >= KIND_INLET) {
+            if (kind >= KIND_INLET && LBM_IN_RANGE(v.aux[slot], v.n_io, 6)) {
                 const int64_t rec = v.aux[slot];
                 const int ax = v.io_axis[rec];
                 const float un = v.io_sign[rec] * (ax == 0 ? M.ux : ax == 1 ? M.uy : M.uz);
@@ -1385,12 +1417,27 @@ cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* 
     }
 }
 
+// LBM_DEBUG: the first failed check's code since the last read (0: none), cleared on read; 0
+// always in the default build
+inline unsigned debug_fault()
+{
+#ifdef LBM_DEBUG
+    unsigned h = 0u;
+    const unsigned zero = 0u;
+    if (cudaMemcpyFromSymbol(&h, g_debug_fault, sizeof(h)) != cudaSuccess) return 0xffffffffu;
+    if (h) cudaMemcpyToSymbol(g_debug_fault, &zero, sizeof(zero));
+    return h;
+#else
+    return 0u;
+#endif
+}
+
 template <int ST>
 const Launchers& make_launchers()
 {
     static const Launchers L = {&launch_step<ST>,        &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
                                 &launch_diagnostics<ST>, &launch_step_batch<ST>, &launch_apply_du<ST>,
-                                &launch_mean_sample<ST>, &launch_probe<ST>};
+                                &launch_mean_sample<ST>, &launch_probe<ST>,       &debug_fault};
     return L;
 }
 

@@ -29,6 +29,20 @@ lbm_status cuda_fail(cudaError_t e, const char* where)
     return fail(LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// LBM_DEBUG builds: STATE if a kernel skipped an out-of-range access (after the stream has
+// been synchronised); the default build returns OK without a device call
+lbm_status debug_status(int storage)
+{
+#ifdef LBM_DEBUG
+    const unsigned code = launchers(storage).debug_fault();
+    if (code)
+        return fail(LBM_ERR_STATE, "LBM_DEBUG: a kernel skipped an out-of-range access (check " + std::to_string(code) + ")");
+#else
+    (void)storage;
+#endif
+    return LBM_OK;
+}
+
 }  // namespace
 
 struct lbm_domain {
@@ -945,6 +959,7 @@ lbm_status lbm_get_diagnostics(lbm_domain* D, lbm_diagnostics* out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, D->d_diag, sizeof(h), cudaMemcpyDeviceToHost, D->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(D->stream);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+    if (lbm_status ds = debug_status(D->params.storage)) return ds;
     h.time = D->time;
     *out = h;
     if (h.n_nonfinite > 0) return fail(LBM_ERR_UNSTABLE, "non-finite populations in " + std::to_string(h.n_nonfinite) + " cells");
@@ -983,7 +998,7 @@ lbm_status lbm_sync(lbm_domain* D)
     if (!D) return fail(LBM_ERR_INVALID_ARG, "NULL domain");
     cudaError_t e = cudaStreamSynchronize(D->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sync");
-    return LBM_OK;
+    return debug_status(D->params.storage);
 }
 
 // ------------------------------------------------------------------------ checkpoints

@@ -134,6 +134,9 @@ struct Launchers {
                                const int32_t* fl_slot, int64_t n_fluid, Sum4* sums, cudaStream_t stream);
     cudaError_t (*probe)(int scheme, const DomainView& v, const void* src, const LevelArgs& a, const int32_t* fl_slot,
                          int64_t n_fluid, const int64_t* idx, int n, float4* out, cudaStream_t stream);
+    // bounds-checked build (LBM_DEBUG): code of the first out-of-range access the kernels of this
+    // storage precision skipped since the last call (0: none; always 0 in the default build)
+    unsigned (*debug_fault)();
 };
 // storage-independent output of the running means (lbm_metrics.cu)
 cudaError_t launch_mean_out(const Sum4* sums, const int32_t* fl_box, int64_t n_fluid, int64_t n_samples, int dense,

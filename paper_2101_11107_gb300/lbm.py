@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "liblbm_gb300.so")
+# LBM_GB300_LIBRARY selects another build of the library (e.g. the bounds-checked LBM_DEBUG
+# variant, _build_debug/liblbm_gb300_debug.so); it must exist like the default one
+LIB_PATH = os.environ.get("LBM_GB300_LIBRARY") or os.path.join(HERE, "_build", "liblbm_gb300.so")
 
 STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSTABLE", 5: "TIMEOUT", 6: "STATE", 7: "IO"}

@@ -144,17 +144,25 @@ class SlabPlan:
                           wave=g.wave, tau_cell=tau_cell, info=dict(g.info, slab=k, slabs=self.n_parts))
 
     # ------------------------------------------------------------------ exchange
-    def transfers(self):
+    def transfers(self, mask=None):
         """One exchange as (source part, source face, destination part, destination face): the
         source packs the populations leaving through its face, the destination unpacks them into
-        the halo layer of its face across the same cut.  Listed in the same order on every rank."""
+        the halo layer of its face across the same cut.  Listed in the same order on every rank.
+        With the global mask, a cut where the layer on either side is solid throughout carries
+        nothing (no cell of that layer pulls across it, and the other side has no halo cells)
+        and is left out."""
+        n = self.ext[self.axis]
         out = []
         for p in self.parts:
             if p.low is not None:
-                out.append((p.low, self.high_face(), p.index, self.low_face()))
+                out.append((p.low, self.high_face(), p.index, self.low_face(), (p.lo - 1) % n, p.lo))
             if p.high is not None:
-                out.append((p.high, self.low_face(), p.index, self.high_face()))
-        return out
+                out.append((p.high, self.low_face(), p.index, self.high_face(), p.hi % n, p.hi - 1))
+        if mask is not None:
+            ax = mask.ndim - 1 - self.axis
+            live = np.take(mask, np.arange(n), axis=ax).astype(bool).any(axis=tuple(d for d in range(3) if d != ax))
+            out = [t for t in out if live[t[4]] and live[t[5]]]
+        return [t[:4] for t in out]
 
     def face_values(self):
         """Values in one exchange buffer: 9 directions x the area of a cut face."""
@@ -162,16 +170,16 @@ class SlabPlan:
         return 9 * a * b
 
 
-def exchange_between_ranks(plan: SlabPlan, rank: int, pack, unpack, make_buf, group=None):
+def exchange_between_ranks(plan: SlabPlan, rank: int, pack, unpack, make_buf, group=None, mask=None):
     """One exchange of the slab held by this rank with its neighbours' ranks (rank k holds part
     k): pack(face, buf) fills a buffer with the populations leaving through a face, unpack(face,
     buf) writes a received buffer into a halo layer, make_buf() gives an empty buffer.  Messages
     carry the destination face as their tag; every rank posts its sends and receives in the
-    order of plan.transfers()."""
+    order of plan.transfers(mask) (mask: the global mask, as every rank has it)."""
     import torch.distributed as dist
 
     ops, recvs = [], []
-    for src, sf, dst, df in plan.transfers():
+    for src, sf, dst, df in plan.transfers(mask):
         if src == rank:
             buf = make_buf()
             pack(sf, buf)
@@ -198,17 +206,18 @@ class SlabDomain:
 
         self.plan = SlabPlan(g.mask.shape, g.periodic, n_parts, axis)
         self.shape = g.mask.shape
+        self.transfers = self.plan.transfers(g.mask)
         self.parts = [lbm.Domain.from_geometry(self.plan.part_geometry(g, k), storage=storage, scheme="ab", **kw)
                       for k in range(n_parts)]
         dtype = torch.int32 if storage == "fp32" else torch.int16
         self.bufs = {}
-        for src, sf, dst, df in self.plan.transfers():
+        for src, sf, dst, df in self.transfers:
             n = self.parts[src].halo_size(sf)
             assert n == self.parts[dst].halo_size(df) == self.plan.face_values()
             self.bufs[(src, sf)] = torch.empty(n, dtype=dtype, device=self.parts[src].device)
 
     def exchange(self):
-        tr = self.plan.transfers()
+        tr = self.transfers
         for src, sf, _, _ in tr:
             self.parts[src].halo_pack(sf, self.bufs[(src, sf)])
         for src, sf, dst, df in tr:

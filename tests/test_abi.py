@@ -204,3 +204,16 @@ def test_autotune_cache_file(tmp_path):
     assert lbm.autotune_cache_get(path, "k1") is None
     lbm.autotune_cache_put(path, "k3", {"best": "128x7", "ms": {}})
     assert set(json.load(open(path))) == {"k3"}
+
+
+def test_debug_variant_compiles(tmp_path):
+    """The bounds-checked variant (-DLBM_DEBUG) of the step kernels and the host code compiles
+    for sm_103a (the GPU test runs it)."""
+    import subprocess
+
+    src = os.path.join(ROOT, "paper_2101_11107_gb300", "csrc")
+    for name in ("lbm_step_fp16.cu", "lbm_domain.cu"):
+        cmd = [lib_build.NVCC, *lib_build.ARCH, *lib_build.FLAGS, "-DLBM_DEBUG", "-c", os.path.join(src, name),
+               "-o", str(tmp_path / (name + ".o"))]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]

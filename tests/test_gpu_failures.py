@@ -169,14 +169,16 @@ def test_corrector_fallback_to_plain_solver():
     bad.set_params(vec)
     rho0, u0 = dom.macroscopic()
     assert S.correct_or_fall_back(dom, bad, None, None, 0.25) is False
-    d = dom.diagnostics()
-    assert d["n_nonfinite"] == 0
-    rho1, u1 = dom.macroscopic()
-    # re-initialised at equilibrium from the state before the correction and re-streamed: the
-    # same macroscopic state up to what streaming moves between neighbours (the flow's own
-    # density and velocity gradients)
-    fl = g.mask > 0
-    assert np.all(np.isfinite(u1)) and np.abs(rho1 - rho0).max() < 1e-2
-    assert np.linalg.norm((u1 - u0)[:, fl]) < 0.1 * np.linalg.norm(u0[:, fl])
-    dom.step(40)
     assert dom.diagnostics()["n_nonfinite"] == 0
+    # the fallback re-initialises every population from the state before the correction: the
+    # same fields, bit for bit, as a twin that never saw the bad network and is re-initialised
+    # from the same rho, u
+    twin = lbm.Domain.from_geometry(g)
+    twin.step(30)
+    assert S.correct_or_fall_back(twin, good, None, None, 0.25) is True
+    twin.init_equilibrium(rho0, u0)
+    assert all(np.array_equal(x, y) for x, y in zip(dom.macroscopic(), twin.macroscopic()))
+    dom.step(40)
+    twin.step(40)
+    assert dom.diagnostics()["n_nonfinite"] == 0
+    assert all(np.array_equal(x, y) for x, y in zip(dom.macroscopic(), twin.macroscopic()))

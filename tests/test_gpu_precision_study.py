@@ -13,10 +13,13 @@ runs the full box and every z-layer is compared.  The study prints one JSON reco
 and the same for the oracle itself against the analytic solution (the discretisation error of
 the halfway bounce-back staircase wall, common to every precision).
 
-Bounds (asserted): FP32 keeps the FP64 result to 1e-4 of max|u| over ten periods (184,723
-steps), FP16 to 2e-2 relative L2; BF16 is reported only: the body force adds 3e-5 per step to
-(f - w)/w ~ 5e-2, far below BF16's half-ulp of 1e-4 there, so BF16 storage cannot represent
-this forcing (the same stall as on the force-driven pipe).
+Errors are normalised by the period: the oscillating flow passes through rest twice a period,
+where an error relative to the instantaneous field divides by almost nothing (the per-phase
+numbers are reported too).  Bounds (asserted): FP32 keeps the FP64 result to 1e-4 of the
+period's peak velocity over ten periods (184,726 steps); FP16 to 2e-2 relative L2 over the
+sampled phases; BF16 is reported only: the body force adds ~3e-5 per step to (f - w)/w ~ 5e-2,
+below BF16's half-ulp of ~1e-4 there, so BF16 storage cannot represent this forcing (the same
+stall as on the force-driven pipe).
 """
 import json
 import math
@@ -84,12 +87,19 @@ def run_study(storages, periods, n_phases):
             rows.append({"t": t,
                          "rel_l2_oracle": float(np.linalg.norm(du) / (np.linalg.norm(ur[fl]) * math.sqrt(uz.shape[0]))),
                          "max_oracle": float(np.abs(du).max() / np.abs(ur[fl]).max()),
+                         "abs_max_oracle": float(np.abs(du).max()), "ref_max": float(np.abs(ur[fl]).max()),
+                         "sq_err": float((du.astype(np.float64) ** 2).sum() / uz.shape[0]),
+                         "sq_ref": float((ur[fl].astype(np.float64) ** 2).sum()),
                          "max_analytic": float(np.abs(uz[:, fl] - ua[fl][None, :]).max() / scale),
                          "finite": bool(np.all(np.isfinite(uz)))})
         dom.close()
         out["storage"][storage] = {
-            "rel_l2_oracle": max(rw["rel_l2_oracle"] for rw in rows),
-            "max_oracle": max(rw["max_oracle"] for rw in rows),
+            # normalised by the period: the oscillating flow passes through rest twice a period,
+            # where a per-phase relative error divides by a near-zero field
+            "period_max_oracle": max(rw["abs_max_oracle"] for rw in rows) / max(rw["ref_max"] for rw in rows),
+            "period_l2_oracle": math.sqrt(sum(rw["sq_err"] for rw in rows) / sum(rw["sq_ref"] for rw in rows)),
+            "phase_rel_l2_oracle_max": max(rw["rel_l2_oracle"] for rw in rows),
+            "phase_max_oracle_max": max(rw["max_oracle"] for rw in rows),
             "max_analytic": max(rw["max_analytic"] for rw in rows),
             "finite": all(rw["finite"] for rw in rows), "samples": rows}
     print("PRECISION_STUDY " + json.dumps(out), flush=True)
@@ -101,16 +111,16 @@ def test_womersley_fp16_one_period():
     oracle at 8 phases of the period."""
     res = run_study(["fp16"], periods=1, n_phases=8)
     s = res["storage"]["fp16"]
-    assert s["finite"] and s["rel_l2_oracle"] <= 2e-2, s
+    assert s["finite"] and s["period_l2_oracle"] <= 2e-2 and s["phase_rel_l2_oracle_max"] <= 3e-2, s
 
 
 def test_womersley_precision_study_ten_periods():
-    """Ten periods (184,723 steps) in FP32, FP16 and BF16, sampled at 10 phases of the last
+    """Ten periods (184,726 steps) in FP32, FP16 and BF16, sampled at 10 phases of the last
     period, against the oracle and the analytic solution."""
     res = run_study(["fp32", "fp16", "bf16"], periods=10, n_phases=10)
     st = res["storage"]
-    assert st["fp32"]["max_oracle"] <= 1e-4, st["fp32"]
-    assert st["fp16"]["finite"] and st["fp16"]["rel_l2_oracle"] <= 2e-2, st["fp16"]
+    assert st["fp32"]["period_max_oracle"] <= 1e-4 and st["fp32"]["period_l2_oracle"] <= 1e-4, st["fp32"]
+    assert st["fp16"]["finite"] and st["fp16"]["period_l2_oracle"] <= 2e-2, st["fp16"]
     assert st["bf16"]["finite"]
     # the FP32 run carries the discretisation error of the oracle and nothing more
     assert abs(st["fp32"]["max_analytic"] - max(res["oracle_vs_analytic"])) <= 1e-3

@@ -155,3 +155,16 @@ def test_exchange_between_gloo_ranks(world, shape, periodic):
         n_recv += 1
     assert n_recv == sum(len(v) for v in res.values())
     assert n_recv == (2 * world if periodic[plan.axis] else 2 * (world - 1))
+
+
+def test_cut_through_solid_layers_carries_nothing():
+    """A cut with a layer that is solid throughout on one side drops both of its transfers: the
+    other side has no halo cells there, and no cell of the solid layer pulls across."""
+    mask = np.zeros((24, 8, 8), np.uint8)
+    mask[0:10, 2:6, 2:6] = 1   # fluid in z = 0..9 only: the cut at z = 12 meets solid layers
+    plan = S.SlabPlan(mask.shape, (0, 0, 0), 2)
+    assert plan.transfers() != [] and plan.transfers(mask) == []
+    g = I.Geometry(mask=mask)
+    assert not np.any(plan.part_geometry(g, 1).mask == S.HALO)
+    mask[11:13, 2:6, 2:6] = 1  # both layers at the cut (z = 11, 12) now hold fluid
+    assert len(plan.transfers(mask)) == 2
