@@ -268,6 +268,22 @@ lbm_status lbm_batch_autotune(lbm_batch* batch, int32_t trial_steps, int32_t* be
 void lbm_batch_destroy(lbm_batch* batch);
 
 /*
+ * Persistent mode of a batch (enable != 0): each chunk of graph_steps steps becomes one
+ * cooperative kernel launch, captured in the chunk's CUDA graph, whose CTAs stay resident for
+ * the whole chunk and advance every member step after step, meeting at a grid-wide barrier
+ * between steps (a member's next step reads what neighbouring CTAs wrote).  Results are the same
+ * bit for bit as one launch per step.  Every wait at a barrier gives up after barrier_timeout_s
+ * seconds (in (0, 3600]; 1.0 is a sensible value): the CTA that gives up flags the chunk, every
+ * CTA leaves at its next barrier, and the next lbm_batch_step or lbm_batch_sync returns
+ * LBM_ERR_TIMEOUT -- the members' populations are then undefined (reload a checkpoint).
+ * enable = 0 returns to one launch per step.  lbm_batch_autotune always times the one-launch
+ * configurations.  Waits for the batch's stream.  Errors: INVALID_ARG, CUDA.
+ * lbm_batch_sync: waits for the batch's work; TIMEOUT if a persistent chunk gave up.
+ */
+lbm_status lbm_batch_set_persistent(lbm_batch* batch, int32_t enable, double barrier_timeout_s);
+lbm_status lbm_batch_sync(lbm_batch* batch);
+
+/*
  * Learned coarse-grid corrector (not part of the paper: its Sec. 3.4 shows that a 2x coarser
  * grid keeps useful accuracy at ~14x less cost; the corrector nudges the coarse velocity toward
  * the fine solution restricted onto the coarse grid).  A 3-layer 3-D convolutional network,

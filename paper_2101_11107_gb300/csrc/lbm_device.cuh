@@ -959,6 +959,88 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     step_cell<ST, LBM_SCHEME_ESOTERIC, COLL, PC>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
 }
 
+// Persistent form of the batched step: one launch advances every domain `steps` steps.  The CTAs
+// (all resident: the launch is cooperative) stride over the concatenated brick list, BRICKS bricks
+// per unit of work, and meet at a grid-wide barrier after each step, since the twist's next step
+// reads what neighbouring CTAs wrote.  Every wait at the barrier is bounded by `limit_ns` of the
+// global timer: a CTA that gives up raises bar->fail and every CTA leaves at its next barrier, so
+// a chunk that cannot complete ends instead of hanging (the host then reports LBM_ERR_TIMEOUT).
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true when every CTA has finished step s; false when this CTA or another gave up
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int target, uint64_t limit_ns)
+{
+    __shared__ int ok;
+    __syncthreads();  // this CTA's writes of the step are done
+    if (threadIdx.x == 0) {
+        int good = 1;
+        __threadfence();  // release them at GPU scope before arriving
+        atomicAdd(&bar->count, 1u);
+        const uint64_t t0 = global_ns();
+        while (true) {
+            unsigned int c, f;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&bar->count) : "memory");
+            if (c >= target) break;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(&bar->fail) : "memory");
+            if (f) {
+                good = 0;
+                break;
+            }
+            if (global_ns() - t0 > limit_ns) {
+                atomicExch(&bar->fail, 1u);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int ST, int BRICKS, int MINB, int COLL, int P0>
+__global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
+    k_step_batch_persistent(const BatchEntry* __restrict__ ent, const int64_t* __restrict__ brick_start, int n_dom,
+                            const LevelArgs* __restrict__ args, int steps, GridBarrier* bar, uint64_t limit_ns)
+{
+    const int64_t total = __ldg(brick_start + n_dom);
+    const int64_t n_units = (total + BRICKS - 1) / BRICKS;
+    for (int s = 0; s < steps; ++s) {
+        for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+            const int64_t gbrick = unit * BRICKS + (threadIdx.x / BRICK_CELLS);
+            if (gbrick < total) {  // whole warps
+                int lo = 0, hi = n_dom - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(brick_start + mid) <= gbrick) lo = mid;
+                    else hi = mid - 1;
+                }
+                const DomainView v = ent[lo].view;
+                const LevelArgs a = args[(size_t)s * n_dom + lo];
+                const uint32_t slot =
+                    (uint32_t)((gbrick - __ldg(brick_start + lo)) * BRICK_CELLS) + (threadIdx.x & 63u);
+                // P0 >= 0: every member has parity P0 at step 0, so step s has parity P0 ^ (s & 1)
+                if (P0 >= 0 && ((s & 1) ^ P0) == 0)
+                    step_cell<ST, LBM_SCHEME_ESOTERIC, COLL, (P0 >= 0 ? 0 : -1)>(v, ent[lo].pop, ent[lo].pop, a, slot,
+                                                                                 threadIdx.x & 31u);
+                else if (P0 >= 0)
+                    step_cell<ST, LBM_SCHEME_ESOTERIC, COLL, (P0 >= 0 ? 1 : -1)>(v, ent[lo].pop, ent[lo].pop, a, slot,
+                                                                                 threadIdx.x & 31u);
+                else
+                    step_cell<ST, LBM_SCHEME_ESOTERIC, COLL, -1>(v, ent[lo].pop, ent[lo].pop, a, slot, threadIdx.x & 31u);
+            }
+        }
+        if (s + 1 < steps && !grid_barrier(bar, (unsigned int)(s + 1) * gridDim.x, limit_ns)) return;
+    }
+}
+
 // Running means (the time averaging of Sec. 3.3): sums[k] += (rho, ux, uy, uz) of fluid cell k at
 // the current level, in FP64 so that thousands of samples add without loss.
 template <int ST, int SCHEME>
@@ -1404,6 +1486,45 @@ cudaError_t launch_step_batch_t(const BatchEntry* ent, const int64_t* brick_star
     });
 }
 
+// one cooperative launch of k_step_batch_persistent (128 threads, 6 CTAs per SM at most): as many
+// CTAs as can be resident, never more than units of work
+template <int ST, int COLL, int P0>
+cudaError_t launch_persistent_t(const BatchEntry* ent, const int64_t* brick_start, int n_dom, int64_t total_bricks,
+                                const LevelArgs* args, int steps, GridBarrier* bar, uint64_t limit_ns, cudaStream_t s)
+{
+    constexpr int BRICKS = 2, MINB = 6;
+    auto k = k_step_batch_persistent<ST, BRICKS, MINB, COLL, P0>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BRICKS * BRICK_CELLS, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t units = (total_bricks + BRICKS - 1) / BRICKS;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)sms * per_sm));
+    void* kargs[] = {(void*)&ent, (void*)&brick_start, (void*)&n_dom, (void*)&args, (void*)&steps, (void*)&bar,
+                     (void*)&limit_ns};
+    return cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(BRICKS * BRICK_CELLS), kargs, 0, s);
+}
+
+template <int ST>
+cudaError_t launch_step_batch_persistent(const BatchEntry* ent, const int64_t* brick_start, int n_dom,
+                                         int64_t total_bricks, const LevelArgs* args, int coll, int parity0, int steps,
+                                         GridBarrier* bar, uint64_t limit_ns, cudaStream_t s)
+{
+    if (total_bricks == 0 || steps == 0) return cudaSuccess;
+    return with_coll(coll, [&](auto c) {
+        constexpr int C = decltype(c)::value;
+        // parity-specialised steps for the default rates when the members share a parity
+        if constexpr (C == COLL_CHM_FAST) {
+            if (parity0 == 0)
+                return launch_persistent_t<ST, C, 0>(ent, brick_start, n_dom, total_bricks, args, steps, bar, limit_ns, s);
+            if (parity0 == 1)
+                return launch_persistent_t<ST, C, 1>(ent, brick_start, n_dom, total_bricks, args, steps, bar, limit_ns, s);
+        }
+        return launch_persistent_t<ST, C, -1>(ent, brick_start, n_dom, total_bricks, args, steps, bar, limit_ns, s);
+    });
+}
+
 template <int ST>
 cudaError_t launch_step_batch(int config, const BatchEntry* ent, const int64_t* brick_start, int n_dom,
                               int64_t total_bricks, const LevelArgs* args, int coll, int parity, cudaStream_t s)
@@ -1437,7 +1558,8 @@ const Launchers& make_launchers()
 {
     static const Launchers L = {&launch_step<ST>,        &launch_macroscopic<ST>, &launch_init_equilibrium<ST>,
                                 &launch_diagnostics<ST>, &launch_step_batch<ST>, &launch_apply_du<ST>,
-                                &launch_mean_sample<ST>, &launch_probe<ST>,       &debug_fault};
+                                &launch_mean_sample<ST>, &launch_probe<ST>,       &debug_fault,
+                                &launch_step_batch_persistent<ST>};
     return L;
 }
 

@@ -1179,7 +1179,13 @@ struct lbm_batch {
     cudaGraphExec_t exec = nullptr;
     int exec_config = -1;
     int exec_parity = -2;  // common parity of the captured chunk's first step (-1: mixed)
+    bool exec_persistent = false;
     cudaEvent_t ev = nullptr;
+    // persistent mode: one cooperative launch per chunk, a bounded grid barrier between steps
+    bool persistent = false;
+    uint64_t limit_ns = 1000000000ull;
+    GridBarrier* d_bar = nullptr;
+    unsigned int* h_fail = nullptr;  // pinned: the barrier's fail word after the last chunk
 
     int n() const { return (int)doms.size(); }
     // the parity all domains have at step k of the argument table, or -1 if they differ
@@ -1222,6 +1228,15 @@ struct lbm_batch {
         cudaError_t e = cudaMemcpyAsync(d_args, h_args, sizeof(LevelArgs) * (size_t)steps * n(), cudaMemcpyHostToDevice,
                                         stream);
         const Launchers& L = launchers(storage);
+        if (persistent) {
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, sizeof(GridBarrier), stream);
+            if (e == cudaSuccess)
+                e = L.step_batch_persistent(d_ent, d_start, n(), total_bricks, d_args, coll, common_parity(0), steps,
+                                            d_bar, limit_ns, stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_fail, &d_bar->fail, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream);
+            return e;
+        }
         for (int k = 0; k < steps && e == cudaSuccess; ++k)
             e = L.step_batch(config, d_ent, d_start, n(), total_bricks, d_args + (size_t)k * n(), coll,
                              common_parity(k), stream);
@@ -1243,15 +1258,19 @@ struct lbm_batch {
         if (g) cudaGraphDestroy(g);
         exec_config = (e == cudaSuccess) ? launch_config : -1;
         exec_parity = (e == cudaSuccess) ? common_parity(0) : -2;
+        exec_persistent = persistent;
         return e;
     }
+    // a persistent chunk that has completed gave up at a barrier
+    bool timed_out() const { return persistent && h_fail && *h_fail != 0u; }
     void release()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (ev) cudaEventDestroy(ev);
         if (stream) cudaStreamDestroy(stream);
         if (h_args) cudaFreeHost(h_args);
-        for (void* p : {(void*)d_ent, (void*)d_start, (void*)d_args})
+        if (h_fail) cudaFreeHost(h_fail);
+        for (void* p : {(void*)d_ent, (void*)d_start, (void*)d_args, (void*)d_bar})
             if (p) owner->dev_free(p, 0);
     }
 };
@@ -1300,12 +1319,15 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
     cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_args, B->args_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_fail, sizeof(unsigned int));
+    if (e == cudaSuccess) *B->h_fail = 0u;
     lbm_status st = (e == cudaSuccess) ? LBM_OK : cuda_fail(e, "batch set-up");
     if (!st) {
         B->d_ent = static_cast<BatchEntry*>(B->owner->dev_alloc(sizeof(BatchEntry) * (size_t)n));
         B->d_start = static_cast<int64_t*>(B->owner->dev_alloc(sizeof(int64_t) * ((size_t)n + 1)));
         B->d_args = static_cast<LevelArgs*>(B->owner->dev_alloc(B->args_bytes));
-        if (!B->d_ent || !B->d_start || !B->d_args) st = fail(LBM_ERR_OOM, "allocation failed: batch tables");
+        B->d_bar = static_cast<GridBarrier*>(B->owner->dev_alloc(sizeof(GridBarrier)));
+        if (!B->d_ent || !B->d_start || !B->d_args || !B->d_bar) st = fail(LBM_ERR_OOM, "allocation failed: batch tables");
     }
     if (!st) {
         e = cudaMemcpyAsync(B->d_ent, ent.data(), sizeof(BatchEntry) * ent.size(), cudaMemcpyHostToDevice, B->stream);
@@ -1339,11 +1361,18 @@ lbm_status lbm_batch_step(lbm_batch* B, int64_t n)
         // the pinned argument table is reused: wait until the previous chunk has read it
         e = cudaStreamSynchronize(B->stream);
         if (e != cudaSuccess) break;
+        if (B->timed_out()) {
+            *B->h_fail = 0u;
+            B->join_to_domains();
+            return fail(LBM_ERR_TIMEOUT, "persistent batch: a grid barrier wait gave up; the members' populations "
+                                         "are undefined");
+        }
         B->fill_args(k);
         if (k == B->graph_steps) {
             // the captured kernels are specialised by parity: recapture if the chunk starts
             // with another one (an odd chunk length, or members stepped on their own)
-            if (!B->exec || B->exec_config != B->launch_config || B->exec_parity != B->common_parity(0))
+            if (!B->exec || B->exec_config != B->launch_config || B->exec_parity != B->common_parity(0) ||
+                B->exec_persistent != B->persistent)
                 e = B->capture();
             if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
         } else {
@@ -1355,6 +1384,33 @@ lbm_status lbm_batch_step(lbm_batch* B, int64_t n)
     }
     if (e == cudaSuccess) e = B->join_to_domains();
     if (e != cudaSuccess) return cuda_fail(e, "batch step");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_persistent(lbm_batch* B, int32_t enable, double barrier_timeout_s)
+{
+    g_last_error.clear();
+    if (!B) return fail(LBM_ERR_INVALID_ARG, "NULL batch");
+    if (!(barrier_timeout_s > 0.0) || !(barrier_timeout_s <= 3600.0))
+        return fail(LBM_ERR_INVALID_ARG, "barrier_timeout_s must be in (0, 3600]");
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch");
+    B->persistent = enable != 0;
+    B->limit_ns = (uint64_t)std::max(1.0, barrier_timeout_s * 1e9);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* B)
+{
+    g_last_error.clear();
+    if (!B) return fail(LBM_ERR_INVALID_ARG, "NULL batch");
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    if (B->timed_out()) {
+        *B->h_fail = 0u;
+        return fail(LBM_ERR_TIMEOUT, "persistent batch: a grid barrier wait gave up; the members' populations are "
+                                     "undefined");
+    }
     return LBM_OK;
 }
 
@@ -1388,6 +1444,8 @@ lbm_status lbm_batch_autotune(lbm_batch* B, int32_t trial_steps, int32_t* best_c
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p + D->pop_bytes(), D->d_side, D->side_bytes(), cudaMemcpyDeviceToDevice, B->stream);
     }
+    const bool was_persistent = B->persistent;
+    B->persistent = false;  // the trial times the one-launch-per-step configurations
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (!st && e == cudaSuccess) e = cudaEventCreate(&t0);
     if (!st && e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -1433,6 +1491,7 @@ lbm_status lbm_batch_autotune(lbm_batch* B, int32_t trial_steps, int32_t* best_c
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     for (auto& k : keep) B->owner->dev_free(k.first, k.second);
+    B->persistent = was_persistent;
     if (e == cudaSuccess) e = B->join_to_domains();
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "batch autotune");

@@ -95,6 +95,12 @@ struct LevelArgs {
     float magic;     // TRT2: Lambda, for cells with their own tau
 };
 
+// Barrier state of a persistent batched launch (cleared before each launch).
+struct GridBarrier {
+    unsigned int count;  // arrivals so far in this launch (step s completes at (s + 1) * gridDim.x)
+    unsigned int fail;   // 1: a wait gave up; the populations are no longer a valid state
+};
+
 // One domain of a batched launch.
 struct BatchEntry {
     DomainView view;
@@ -137,6 +143,12 @@ struct Launchers {
     // bounds-checked build (LBM_DEBUG): code of the first out-of-range access the kernels of this
     // storage precision skipped since the last call (0: none; always 0 in the default build)
     unsigned (*debug_fault)();
+    // persistent batched step: `steps` steps of every domain in one cooperative launch, a grid
+    // barrier (waits bounded by limit_ns) between steps; args[s][d]; parity0: the parity every
+    // domain has at step 0, or -1
+    cudaError_t (*step_batch_persistent)(const BatchEntry* ent, const int64_t* brick_start, int n_dom,
+                                         int64_t total_bricks, const LevelArgs* args, int coll, int parity0, int steps,
+                                         GridBarrier* bar, uint64_t limit_ns, cudaStream_t stream);
 };
 // storage-independent output of the running means (lbm_metrics.cu)
 cudaError_t launch_mean_out(const Sum4* sums, const int32_t* fl_box, int64_t n_fluid, int64_t n_samples, int dense,

@@ -29,7 +29,8 @@ EXPORTS = ["lbm_default_params", "lbm_create_domain", "lbm_set_inlet_waveform", 
            "lbm_corrector_create", "lbm_corrector_get_params", "lbm_corrector_set_params", "lbm_corrector_forward",
            "lbm_corrector_gradients", "lbm_corrector_train_step", "lbm_corrector_apply", "lbm_corrector_destroy",
            "lbm_apply_velocity_correction", "lbm_restrict", "lbm_mean_reset", "lbm_mean_sample", "lbm_mean_get",
-           "lbm_probe", "lbm_similarity_index", "lbm_halo_size", "lbm_halo_pack", "lbm_halo_unpack"]
+           "lbm_probe", "lbm_similarity_index", "lbm_halo_size", "lbm_halo_pack", "lbm_halo_unpack",
+           "lbm_batch_set_persistent", "lbm_batch_sync"]
 N_LAUNCH_CONFIGS = 8
 LAUNCH_CONFIG_NAMES = ["256x3", "128x7", "128x6", "128x8", "128x10", "pipe128x6", "2c128x4", "2c128x3"]
 SCHEME = {"ab": 0, "esoteric": 1}
@@ -108,6 +109,8 @@ def load_library(path: str = LIB_PATH):
     L.lbm_batch_step.argtypes = [vp, i64]
     L.lbm_batch_set_launch_config.argtypes = [vp, i32]
     L.lbm_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+    L.lbm_batch_set_persistent.argtypes = [vp, i32, dbl]
+    L.lbm_batch_sync.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     L.lbm_corrector_num_params.argtypes = []
@@ -140,7 +143,7 @@ def load_library(path: str = LIB_PATH):
                  "lbm_get_diagnostics_noalloc", "lbm_batch_create", "lbm_batch_step",
                  "lbm_batch_set_launch_config", "lbm_batch_autotune", "lbm_mean_reset", "lbm_mean_sample",
                  "lbm_mean_get", "lbm_probe", "lbm_similarity_index", "lbm_halo_size", "lbm_halo_pack",
-                 "lbm_halo_unpack"]:
+                 "lbm_halo_unpack", "lbm_batch_set_persistent", "lbm_batch_sync"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -630,6 +633,15 @@ class Batch:
         ms = (ctypes.c_float * N_LAUNCH_CONFIGS)()
         _check(load_library().lbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(best), ms))
         return best.value, dict(zip(LAUNCH_CONFIG_NAMES, list(ms)))
+
+    def set_persistent(self, enable=True, barrier_timeout_s=1.0):
+        """One cooperative launch per graph chunk with a bounded grid barrier between steps
+        (lbm_batch_set_persistent)."""
+        _check(load_library().lbm_batch_set_persistent(self._h, int(bool(enable)), float(barrier_timeout_s)))
+
+    def sync(self):
+        """Waits for the batch; raises LbmError (TIMEOUT) if a persistent chunk gave up."""
+        _check(load_library().lbm_batch_sync(self._h))
 
     @property
     def n_fluid(self):

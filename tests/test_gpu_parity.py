@@ -512,3 +512,63 @@ def test_autotune_cache_hit_skips_timing(tmp_path):
     c = lbm.Domain.from_geometry(g, storage="fp16")
     c.autotune(5, cache=path)
     assert c.autotuned_from_cache is False
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_persistent_batch_equals_separate_domains(storage):
+    """Persistent mode (one cooperative launch per chunk, grid barrier between steps): two
+    captured chunks of 10 steps and an uncaptured remainder of 7, with one member started 3 steps
+    earlier (mixed parities: runtime-parity kernel), then 20 more with uniform parities (the
+    parity-specialised kernel); fields equal each domain stepped alone, bit for bit."""
+    gs, doms = _batch_members(storage)
+    _, alone = _batch_members(storage)
+    doms[1].step(3)
+    alone[1].step(3)
+    batch = lbm.Batch(doms, graph_steps=10)
+    batch.set_persistent(True, 1.0)
+    batch.step(27)
+    batch.sync()
+    for d, a in zip(doms, alone):
+        a.step(27)
+        assert d.time == a.time
+        assert np.array_equal(d.macroscopic()[1], a.macroscopic()[1])
+    for d, a in zip(doms, alone):  # member 1 is at 30, the others at 27: one step brings all to even
+        if d is not doms[1]:
+            d.step(1)
+            a.step(1)
+    assert len({d.time % 2 for d in doms}) == 1
+    batch.step(20)
+    batch.sync()
+    for d, a in zip(doms, alone):
+        a.step(20)
+        assert np.array_equal(d.macroscopic()[0], a.macroscopic()[0])
+        assert np.array_equal(d.macroscopic()[1], a.macroscopic()[1])
+    batch.close()
+
+
+def test_persistent_batch_barrier_gives_up():
+    """With a barrier limit of one nanosecond no grid barrier can be met: the chunk ends (it does
+    not hang), the batch reports TIMEOUT, and the GPU stays usable -- a fresh batch of fresh
+    domains then runs and matches separate domains."""
+    import time
+
+    gs, doms = _batch_members("fp32")
+    batch = lbm.Batch(doms, graph_steps=10)
+    batch.set_persistent(True, 1e-9)
+    t0 = time.time()
+    batch.step(10)
+    with pytest.raises(lbm.LbmError) as e:
+        batch.sync()
+    assert e.value.status == 5 and time.time() - t0 < 30
+    batch.set_persistent(True, 1.0)
+    batch.close()
+    _, fresh = _batch_members("fp32")
+    _, alone = _batch_members("fp32")
+    b2 = lbm.Batch(fresh, graph_steps=10)
+    b2.set_persistent(True, 1.0)
+    b2.step(10)
+    b2.sync()
+    for d, a in zip(fresh, alone):
+        a.step(10)
+        assert np.array_equal(d.macroscopic()[1], a.macroscopic()[1])
+    b2.close()
