@@ -6,12 +6,17 @@ One benchmark step = one lattice Boltzmann time step over every fluid cell (one 
 fused kernel).  Before every timed step, outside the timed region, the L2 cache is flushed by
 writing a 512 MB buffer and then reading another 512 MB buffer (so that the flush's own dirty
 lines are written back before the step starts): every step streams its populations from HBM
-into a clean, cold L2.  A larger-than-L2 workload (the seeded synthetic aneurysm at 512^3) is
-also timed back to back as a variant.
+into a clean, cold L2 (the FP32 state, 100 MB, fits in the 129 MB L2: the line says so).  The
+larger-than-L2 anchor, the seeded synthetic aneurysm at 512^3 (FP32 state 215 MB), is timed back
+to back and reported as its own roofline object.  Variants: FP16 / BF16 storage, the A-B scheme,
+the SRT / TRT operators, 16 batched aneurysms (graph of launches, persistent launch, and 16
+sequential runs), and the coarse grid + learned corrector comparison (errors and wall times of
+fine, coarse and coarse + corrector runs, and the plain resolution of equal error).
 
-Metric: fluid MLUPS (million fluid-cell updates per second) and the fraction of the measured HBM
-copy bandwidth achieved with the algorithmic 27 reads + 27 writes per update (216 B in FP32,
-108 B in FP16/BF16).
+Metric: fluid MLUPS (million fluid-cell updates per second) and the fraction of the HBM roofline
+achieved with the algorithmic 27 reads + 27 writes per update (216 B in FP32, 108 B in
+FP16/BF16): `frac` against the measured copy bandwidth, `frac_of_8tbs` against the metric's
+8 TB/s.
 
 Arms:
   default            the CUDA library (this repository), FP32 storage as the headline, FP16 and
@@ -196,13 +201,26 @@ def batched_variant(steps, flush, clean, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1)
+    # the same batch as one persistent cooperative launch per graph chunk (grid barrier between
+    # steps)
+    batch.set_persistent(True, 1.0)
+    batch.step(graph_steps)  # capture + warm-up
+    batch.sync()
+    flush_l2(flush, clean)
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch.sync()
+    t_pers = e0.elapsed_time(e1)
     batch.close()
     for d in doms:
         d.close()
     return {"domains": len(doms), "edges": edges, "fluid_cells": nf, "steps": steps,
             "batched_graph_mlups": nf * steps / (t_batch * 1e-3) / 1e6,
+            "persistent_graph_mlups": nf * steps / (t_pers * 1e-3) / 1e6,
             "sequential_mlups": nf * steps / (t_seq * 1e-3) / 1e6,
-            "speedup": t_seq / t_batch, "batched_ms": t_batch, "sequential_ms": t_seq,
+            "speedup": t_seq / t_batch, "batched_ms": t_batch, "persistent_ms": t_pers, "sequential_ms": t_seq,
             "launch_config": lbm.LAUNCH_CONFIG_NAMES[best], "graph_steps": graph_steps}
 
 
@@ -238,6 +256,29 @@ def large_variant(stream, steps=100):
             "working_set_over_l2": info["device_bytes"] / l2, "launch_config": lbm.LAUNCH_CONFIG_NAMES[best],
             "timing": "back to back (working set larger than L2)"}
         dom.close()
+    return out
+
+
+def corrector_variant(test_seeds=(200, 201, 202, 203), compare_edges=(144, 160)):
+    """The coarse grid + learned corrector comparison (synthetic aneurysms, fine 256^3 / coarse
+    128^3, Re 300, 32 training geometries, corrector trained on the GPU with 4 rounds of in-loop
+    data), evaluated on held-out geometries: relative L2 error of u against the restricted fine
+    run, wall times of the fine, plain coarse and coarse + corrector runs (CUDA events, one
+    geometry at a time), and the resolution at which the plain solver reaches coarse +
+    corrector's error with its wall time (plain runs at intermediate resolutions)."""
+    from paper_2101_11107_gb300 import corrector_study as S
+
+    t0 = time.perf_counter()
+    summary, _ = S.run(fine_edge=256, period_f=4000, reynolds=300.0, train_seeds=list(range(100, 132)),
+                       test_seeds=list(test_seeds), periods=3, samples_per_period=10, train_steps=4000, lr=1e-3,
+                       apply_every=50, workers=16, log=lambda m: None, dagger_rounds=4,
+                       compare_edges=tuple(compare_edges))
+    keys = ("err_plain_mean", "err_corrected_mean", "err_output_corrected_mean", "si_plain_mean",
+            "si_corrected_mean", "wall_fine_s", "wall_coarse_s", "wall_coarse_corrector_s", "train_s")
+    out = {k: summary[k] for k in keys}
+    out.update({"test_geometries": len(test_seeds), "training_geometries": 32, "equal_error": summary["equal_error"],
+                "study_wall_s": time.perf_counter() - t0,
+                "fallbacks": sum(r["fallback_at_step"] is not None for r in summary["per_geometry"])})
     return out
 
 
@@ -393,6 +434,7 @@ def main():
 
     batch_result = None if args.no_variants else batched_variant(200, flush, clean, stream)
     large_result = None if args.no_variants else large_variant(stream)
+    corrector_result = None if (args.no_variants or world > 1) else corrector_variant()
 
     cpu = None
     if rank == 0 and world == 1:
@@ -445,6 +487,8 @@ def main():
         batch_result["roofline_frac"] = round(bb / hbm_peak, 4)
         batch_result["roofline_frac_of_8tbs"] = round(bb / NOMINAL_HBM_GBS, 4)
         line["variants"]["batch16_aneurysm_fp16"] = batch_result
+    if corrector_result is not None:
+        line["variants"]["coarse_corrector_aneurysm256"] = corrector_result
     if large_result is not None:
         for k, r in large_result.items():
             r["roofline_frac"] = round(r["achieved_gbs"] / hbm_peak, 4)

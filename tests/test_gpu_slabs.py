@@ -23,7 +23,8 @@ def _compare(g, n_parts, steps, storage="fp32", init=None, axis=None):
     whole = lbm.Domain.from_geometry(g, storage=storage, scheme="ab")
     split = S.SlabDomain(g, n_parts, axis=axis, storage=storage)
     assert sum(d.info()["n_fluid"] for d in split.parts) == whole.info()["n_fluid"] == g.nfluid
-    assert all(d.info()["n_halo"] > 0 for d in split.parts)
+    # a slab whose cuts meet solid layers on the far side has no halo cells there
+    assert sum(d.info()["n_halo"] for d in split.parts) > 0
     if init is not None:
         whole.init_equilibrium(*init)
         split.init_equilibrium(*init)
