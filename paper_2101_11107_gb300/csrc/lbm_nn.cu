@@ -277,11 +277,15 @@ __global__ void __launch_bounds__(128)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase) : "memory");
 }
 
-// dW[o][co][ci] += sum_p dy[p][co] x[p + o][ci] and db[co] += sum_p dy[p][co] over the tiles;
-// each warp owns offsets warp, warp + 4, ...; one atomic per weight per CTA at the end.
+// Partial weight gradient of this CTA's tiles: part[blockIdx.x] = (dW[o][co][ci] = sum_p dy[p][co]
+// x[p + o][ci], db[co] = sum_p dy[p][co]) over the tiles blockIdx.x, + gridDim.x, ...; each warp
+// owns offsets warp, warp + 4, ...  The partials are summed over the CTAs in a fixed order by
+// k_wgrad_reduce, so that a training run is reproducible bit for bit (float atomics would sum
+// them in whatever order the CTAs finish).
+constexpr int WG_CTAS = 304;  // weight-gradient CTAs (2 per SM): the partial buffer's depth
 __global__ void __launch_bounds__(128)
     k_wgrad(const __nv_bfloat16* __restrict__ dy, const __nv_bfloat16* __restrict__ x, const int4* __restrict__ tiles,
-            int n_tiles, Box b, float* __restrict__ dW, float* __restrict__ db)
+            int n_tiles, Box b, float* __restrict__ part)
 {
     __shared__ __align__(16) __nv_bfloat16 sdy[64 * CH];
     __shared__ __align__(16) __nv_bfloat16 sx[216 * CH];
@@ -343,6 +347,7 @@ __global__ void __launch_bounds__(128)
             }
         }
     }
+    float* dW = part + (size_t)blockIdx.x * (NW + CH);
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
         const int o = warp + 4 * l;
@@ -350,13 +355,25 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int ci = 8 * j + 2 * t;
-            atomicAdd(&dW[(o * CH + g) * CH + ci], acc[l][j][0]);
-            atomicAdd(&dW[(o * CH + g) * CH + ci + 1], acc[l][j][1]);
-            atomicAdd(&dW[(o * CH + g + 8) * CH + ci], acc[l][j][2]);
-            atomicAdd(&dW[(o * CH + g + 8) * CH + ci + 1], acc[l][j][3]);
+            dW[(o * CH + g) * CH + ci] = acc[l][j][0];
+            dW[(o * CH + g) * CH + ci + 1] = acc[l][j][1];
+            dW[(o * CH + g + 8) * CH + ci] = acc[l][j][2];
+            dW[(o * CH + g + 8) * CH + ci + 1] = acc[l][j][3];
         }
     }
-    if (threadIdx.x < CH) atomicAdd(&db[threadIdx.x], dbacc);
+    if (threadIdx.x < CH) dW[NW + threadIdx.x] = dbacc;
+}
+
+// out[k] = sum over the n_part partial gradients of part[p][k] in increasing p (weights and
+// biases of one layer, NW + CH values).
+__global__ void __launch_bounds__(256)
+    k_wgrad_reduce(const float* __restrict__ part, int n_part, float* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NW + CH) return;
+    float s = 0.0f;
+    for (int p = 0; p < n_part; ++p) s += part[(size_t)p * (NW + CH) + k];
+    out[k] = s;
 }
 
 // The elementwise kernels of the corrector run over the slabs of the convolutions (one CTA of
@@ -579,6 +596,7 @@ struct lbm_corrector {
     float* o4 = nullptr;
     float *rho = nullptr, *u = nullptr, *du = nullptr;  // staging on the coarse box
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    float* wpart = nullptr;  // [WG_CTAS][NW + CH] partial weight gradients of one layer
     __nv_bfloat16 *wb = nullptr, *wt = nullptr;
     double* loss = nullptr;
     unsigned long long* count = nullptr;
@@ -657,18 +675,19 @@ struct lbm_corrector {
             k_loss<<<(unsigned)n_slabs, 128, 0, stream>>>(o4, uu, ut, mk, box, 1.0f / du_scale, count, dO, loss, slabs);
         }
         e = cudaGetLastError();
-        const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_tiles, 1), 304);
-        if (e == cudaSuccess && n_tiles)
-            k_wgrad<<<wg, 128, 0, stream>>>(dO, y2, tiles, (int)n_tiles, box, grad + 2 * (NW + CH), grad + 2 * (NW + CH) + NW);
-        if (e == cudaSuccess) e = cudaGetLastError();
+        const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_tiles, 1), WG_CTAS);
+        // weight gradient of one layer: per-CTA partials, then their sum in a fixed order
+        auto wgrad = [&](const __nv_bfloat16* g, const __nv_bfloat16* xin, float* out) {
+            if (!n_tiles) return cudaSuccess;
+            k_wgrad<<<wg, 128, 0, stream>>>(g, xin, tiles, (int)n_tiles, box, wpart);
+            k_wgrad_reduce<<<blocks(NW + CH, 256), 256, 0, stream>>>(wpart, wg, out);
+            return cudaGetLastError();
+        };
+        if (e == cudaSuccess) e = wgrad(dO, y2, grad + 2 * (NW + CH));
         if (e == cudaSuccess) e = conv(dO, wt + 2 * NW, nullptr, 0, y2, dy2, false);  // dz2 = W3^T dO, gated by y2 > 0
-        if (e == cudaSuccess && n_tiles)
-            k_wgrad<<<wg, 128, 0, stream>>>(dy2, y1, tiles, (int)n_tiles, box, grad + (NW + CH), grad + (NW + CH) + NW);
-        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = wgrad(dy2, y1, grad + (NW + CH));
         if (e == cudaSuccess) e = conv(dy2, wt + NW, nullptr, 0, y1, dy, false);  // dz1 = W2^T dz2, gated by y1 > 0
-        if (e == cudaSuccess && n_tiles)
-            k_wgrad<<<wg, 128, 0, stream>>>(dy, x0, tiles, (int)n_tiles, box, grad, grad + NW);
-        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = wgrad(dy, x0, grad);
         return e;
     }
     cudaError_t prepare()
@@ -771,6 +790,7 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
     K->grad = static_cast<float*>(D(sizeof(float) * NP));
     K->m = static_cast<float*>(D(sizeof(float) * NP));
     K->v = static_cast<float*>(D(sizeof(float) * NP));
+    K->wpart = static_cast<float*>(D(sizeof(float) * (size_t)WG_CTAS * (NW + CH)));
     K->wb = static_cast<__nv_bfloat16*>(D(sizeof(__nv_bfloat16) * 3 * NW));
     K->wt = static_cast<__nv_bfloat16*>(D(sizeof(__nv_bfloat16) * 3 * NW));
     K->loss = static_cast<double*>(D(sizeof(double)));

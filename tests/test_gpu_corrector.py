@@ -262,3 +262,19 @@ def test_trained_corrector_gains_over_plain_coarse():
     assert summary["err_corrected_mean"] < summary["err_plain_mean"], summary
     assert all(r["fallback_at_step"] is None for r in summary["per_geometry"])
     assert summary["wall_coarse_corrector_s"] < summary["wall_fine_s"]
+
+
+def test_training_is_reproducible():
+    """The weight gradients are summed over the CTAs in a fixed order (no float atomics), so two
+    training runs from the same parameters on the same samples end with the same parameters,
+    bit for bit."""
+    mask, rho, u, ut, params = _multi_slab_case(2)
+    tr, tu, tt = _t(rho), _t(u), _t(ut)
+    out = []
+    for _ in range(2):
+        net = lbm.Corrector(mask, params, US, RS, DS)
+        for _ in range(20):
+            net.train_step(tr, tu, tt, 1e-3)
+        out.append(net.params())
+        net.close()
+    assert np.array_equal(out[0], out[1])
