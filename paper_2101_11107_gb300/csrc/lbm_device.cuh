@@ -242,44 +242,6 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
     }
 }
 
-// The same reads as fetch_et / fetch_ab_shfl, returning the raw 16-bit values (h = d / w in FP16
-// or BF16 bits) of a 16-bit state.
-template <bool RW, int PC = -1>
-__device__ __forceinline__ void fetch_et_raw(const void* pop, uint32_t n, const uint32_t (&cs)[8], uint32_t wm,
-                                             int parity, uint16_t (&h)[Q], bool clean = false)
-{
-    const uint16_t* p = static_cast<const uint16_t*>(pop);
-    if (PC >= 0) parity = PC;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const uint32_t flip = (PC >= 0 && clean) ? (uint32_t)PC : (((uint32_t)parity ^ (wm >> i)) & 1u);
-        const uint32_t dir = flip ? (uint32_t)(Q - 1 - i) : (uint32_t)i;
-        const uint32_t off = dir * n + cs[corner_neg(i)];
-        h[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? p[off] : __ldg(reinterpret_cast<const unsigned short*>(p) + off))
-                                                    : (uint16_t)0;
-    }
-}
-
-__device__ __forceinline__ void fetch_ab_shfl_raw(const void* __restrict__ src, uint32_t n, int32_t row_lane,
-                                                  uint32_t slot, uint32_t wm, bool fluid, uint16_t (&h)[Q])
-{
-    const int l = (int)(slot & (BRICK_CELLS - 1));
-    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
-        const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-        const uint32_t nb = (uint32_t)__shfl_sync(0xffffffffu, row_lane, ob);
-        const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
-        const bool wall = (wm >> i) & 1u;
-        const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
-        if (fluid)
-            h[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1)
-                       ? __ldg(reinterpret_cast<const unsigned short*>(src) + off)
-                       : (uint16_t)0;
-    }
-}
-
 // Esoteric twist write after a step of parity P: f*_i to slot (P ? i : opp(i)) of cell x + p_i
 // (PC >= 0: the parity fixed at compile time; X: d carries the factors 2^nnz(c_i)).
 template <int ST, int PC = -1, bool X = false>
@@ -572,15 +534,8 @@ __device__ __forceinline__ void inv3_t(typename L::V& m0, typename L::V& m1, typ
     m1 = g0;
 }
 
-// Raw moments of the deviations up to second order, from the three passes of 1-D sums
-// (S0 = g- + g0 + g+, S1 = g+ - g-, S2 = g+ + g- along x, then along y and z).
-template <class L>
-struct RawMoments {
-    typename L::V drho, jx, jy, jz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
-};
-
-template <class L>
-__device__ __forceinline__ RawMoments<L> raw_moments_d(const typename L::V (&d)[Q])
+template <class L, bool DEFER = false>
+__device__ __forceinline__ void collide_fast_t(typename L::V (&d)[Q], typename L::V s2, const float g[3])
 {
     using V = typename L::V;
     V S0[9], S1[9], S2[9];
@@ -600,134 +555,16 @@ __device__ __forceinline__ RawMoments<L> raw_moments_d(const typename L::V (&d)[
         U1[z] = L::sub(S1[3 * z + 2], S1[3 * z]);
         W[z] = L::add(L::add(S2[3 * z], S2[3 * z + 1]), S2[3 * z + 2]);
     }
-    RawMoments<L> m;
-    m.drho = L::add(L::add(T0[0], T0[1]), T0[2]);
-    m.jz = L::sub(T0[2], T0[0]);
-    m.Pzz = L::add(T0[2], T0[0]);
-    m.jy = L::add(L::add(T1[0], T1[1]), T1[2]);
-    m.Pyz = L::sub(T1[2], T1[0]);
-    m.Pyy = L::add(L::add(T2[0], T2[1]), T2[2]);
-    m.jx = L::add(L::add(U0[0], U0[1]), U0[2]);
-    m.Pxz = L::sub(U0[2], U0[0]);
-    m.Pxy = L::add(L::add(U1[0], U1[1]), U1[2]);
-    m.Pxx = L::add(L::add(W[0], W[1]), W[2]);
-    return m;
-}
-
-// The same raw moments from the stored scaled deviations h_i = d_i / w_i of a 16-bit state,
-// without multiplying each value by its weight: w_i = w(cx) w(cy) w(cz) with the per-axis
-// weights (1, 4, 1) / 6, so each pass sums g- + 4 g0 + g+ (one FMA) instead of g- + g0 + g+,
-// and the ten moments are scaled by 1/216 at the end.  `first` gives the x-pass of one line from
-// its three raw values, as mixed-precision instructions that read the 16-bit values directly
-// (add/sub/fma .f32.f16 or .f32.bf16 of sm_100+: the value is converted exactly inside the
-// instruction, so the rounding is that of the FP32 operation on the converted value).
-template <class L>
-__device__ __forceinline__ typename L::V fma4(typename L::V b, typename L::V c)
-{
-    return L::fma(L::splat(4.0f), b, c);  // 4 b + c, one rounding
-}
-
-template <class L, class XPass>
-__device__ __forceinline__ RawMoments<L> raw_moments_h(XPass first)
-{
-    using V = typename L::V;
-    V S0[9], S1[9], S2[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) first(k, S0[k], S1[k], S2[k]);
-    V T0[3], T1[3], T2[3], U0[3], U1[3], W[3];
-#pragma unroll
-    for (int z = 0; z < 3; ++z) {
-        T2[z] = L::add(S0[3 * z], S0[3 * z + 2]);
-        T0[z] = fma4<L>(S0[3 * z + 1], T2[z]);
-        T1[z] = L::sub(S0[3 * z + 2], S0[3 * z]);
-        U0[z] = fma4<L>(S1[3 * z + 1], L::add(S1[3 * z], S1[3 * z + 2]));
-        U1[z] = L::sub(S1[3 * z + 2], S1[3 * z]);
-        W[z] = fma4<L>(S2[3 * z + 1], L::add(S2[3 * z], S2[3 * z + 2]));
-    }
-    const V k216 = L::splat(1.0f / 216.0f);
-    RawMoments<L> m;
-    m.drho = L::mul(fma4<L>(T0[1], L::add(T0[0], T0[2])), k216);
-    m.jz = L::mul(L::sub(T0[2], T0[0]), k216);
-    m.Pzz = L::mul(L::add(T0[2], T0[0]), k216);
-    m.jy = L::mul(fma4<L>(T1[1], L::add(T1[0], T1[2])), k216);
-    m.Pyz = L::mul(L::sub(T1[2], T1[0]), k216);
-    m.Pyy = L::mul(fma4<L>(T2[1], L::add(T2[0], T2[2])), k216);
-    m.jx = L::mul(fma4<L>(U0[1], L::add(U0[0], U0[2])), k216);
-    m.Pxz = L::mul(L::sub(U0[2], U0[0]), k216);
-    m.Pxy = L::mul(fma4<L>(U1[1], L::add(U1[0], U1[2])), k216);
-    m.Pxx = L::mul(fma4<L>(W[1], L::add(W[0], W[2])), k216);
-    return m;
-}
-
-// Mixed-precision arithmetic on one raw 16-bit value a (FP16 or BF16 bits) and an FP32 value.
-template <int ST>
-struct Mixed;
-template <>
-struct Mixed<LBM_STORE_FP16> {
-    static __device__ __forceinline__ float cvt(uint16_t a) { return __half2float(__ushort_as_half(a)); }
-    static __device__ __forceinline__ float add(uint16_t a, float c)
-    {
-        float r;
-        asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(a), "f"(c));
-        return r;
-    }
-    static __device__ __forceinline__ float sub(uint16_t a, float c)  // a - c
-    {
-        float r;
-        asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(a), "f"(c));
-        return r;
-    }
-    static __device__ __forceinline__ float fma4(uint16_t a, float c)  // 4 a + c
-    {
-        float r;
-        asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(r) : "h"(a), "h"((uint16_t)0x4400), "f"(c));
-        return r;
-    }
-};
-template <>
-struct Mixed<LBM_STORE_BF16> {
-    static __device__ __forceinline__ float cvt(uint16_t a) { return __bfloat162float(__ushort_as_bfloat16(a)); }
-    static __device__ __forceinline__ float add(uint16_t a, float c)
-    {
-        float r;
-        asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(a), "f"(c));
-        return r;
-    }
-    static __device__ __forceinline__ float sub(uint16_t a, float c)
-    {
-        float r;
-        asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(a), "f"(c));
-        return r;
-    }
-    static __device__ __forceinline__ float fma4(uint16_t a, float c)
-    {
-        float r;
-        asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(r) : "h"(a), "h"((uint16_t)0x4080), "f"(c));
-        return r;
-    }
-};
-
-// x-pass of line k from raw 16-bit values: s2 = h+ + h-, s1 = h+ - h-, s0 = 4 h0 + s2
-template <int ST>
-__device__ __forceinline__ RawMoments<Lane1> raw_moments_h1(const uint16_t (&h)[Q])
-{
-    return raw_moments_h<Lane1>([&](int k, float& s0, float& s1, float& s2) {
-        const float hm = Mixed<ST>::cvt(h[3 * k]);
-        s2 = Mixed<ST>::add(h[3 * k + 2], hm);
-        s1 = Mixed<ST>::sub(h[3 * k + 2], hm);
-        s0 = Mixed<ST>::fma4(h[3 * k + 1], s2);
-    });
-}
-
-// Second half of the fast collision: from the raw moments to the post-collision deviations d
-// (DEFER: multiplied by 2^nnz(c_i), for Store::store_x).
-template <class L, bool DEFER = false>
-__device__ __forceinline__ void collide_fast_finish(typename L::V (&d)[Q], const RawMoments<L>& rm, typename L::V s2,
-                                                    const float g[3])
-{
-    using V = typename L::V;
-    const V drho = rm.drho, jx = rm.jx, jy = rm.jy, jz = rm.jz, Pxx = rm.Pxx, Pyy = rm.Pyy, Pzz = rm.Pzz,
-            Pxy = rm.Pxy, Pxz = rm.Pxz, Pyz = rm.Pyz;
+    const V drho = L::add(L::add(T0[0], T0[1]), T0[2]);
+    const V jz = L::sub(T0[2], T0[0]);
+    const V Pzz = L::add(T0[2], T0[0]);
+    const V jy = L::add(L::add(T1[0], T1[1]), T1[2]);
+    const V Pyz = L::sub(T1[2], T1[0]);
+    const V Pyy = L::add(L::add(T2[0], T2[1]), T2[2]);
+    const V jx = L::add(L::add(U0[0], U0[1]), U0[2]);
+    const V Pxz = L::sub(U0[2], U0[0]);
+    const V Pxy = L::add(L::add(U1[0], U1[1]), U1[2]);
+    const V Pxx = L::add(L::add(W[0], W[1]), W[2]);
     const V rho = L::one_plus(drho);
     const V ir = L::rcp1p(drho);
     const V ux = L::fma(jx, ir, L::splat(0.5f * g[0]));
@@ -781,13 +618,6 @@ __device__ __forceinline__ void collide_fast_finish(typename L::V (&d)[Q], const
         for (int p = 0; p < 3; ++p) inv3_t<L, DEFER>(d[p + 9 * r], d[p + 3 + 9 * r], d[p + 6 + 9 * r], uy, yc, y2);
 #pragma unroll
     for (int k = 0; k < 9; ++k) inv3_t<L, DEFER>(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, xc, x2);
-}
-
-template <class L, bool DEFER = false>
-__device__ __forceinline__ void collide_fast_t(typename L::V (&d)[Q], typename L::V s2, const float g[3])
-{
-    const RawMoments<L> m = raw_moments_d<L>(d);
-    collide_fast_finish<L, DEFER>(d, m, s2, g);
 }
 
 template <bool DEFER = false>
@@ -919,34 +749,15 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
     float d[Q];
     LevelArgs la = a;
     if (word & WORD_OWN_TAU) set_own_rate<COLL>(la, __ldg(v.s2_cell + slot));
-    // 16-bit storage with the default rates: a plain cell (no Bouzidi or open-boundary rule to
-    // apply, halfway bounce-back being in the load address) takes its moments straight from the
-    // stored h = d / w (raw_moments_h); other cells convert to d and apply their rules
-    constexpr bool HRAW = X && ST != LBM_STORE_FP32;
-    const bool plain = ((word >> WORD_KIND_SHIFT) & 3u) == KIND_PLAIN;
     if (SCHEME == LBM_SCHEME_ESOTERIC) {
         const int32_t row = __ldg(v.nb8 + brick * 8u + (lane & 7u));
         uint32_t cs[8];
         corner_slots_shfl(row, slot, cs);
         const bool clean = PC >= 0 && __all_sync(0xffffffffu, wm == 0u);
         if (!fluid) return;
-        uint32_t half = 0u;
-        if constexpr (HRAW) {
-            uint16_t h[Q];
-            fetch_et_raw<true, PC>(dst, n, cs, wm, a.parity, h, clean);
-            if (plain) {
-                collide_fast_finish<Lane1, true>(d, raw_moments_h1<ST>(h), la.s2, la.g);
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = w_of(i) * Mixed<ST>::cvt(h[i]);
-                half = wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d);
-                collide_model<COLL, X>(d, la);
-            }
-        } else {
-            fetch_et<ST, true, PC>(dst, n, cs, wm, a.parity, d, clean);
-            half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
-            collide_model<COLL, X>(d, la);
-        }
+        fetch_et<ST, true, PC>(dst, n, cs, wm, a.parity, d, clean);
+        const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
+        collide_model<COLL, X>(d, la);
         store_et<ST, PC, X>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t off = (uint32_t)v.aux[slot];
@@ -959,24 +770,10 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         }
     } else {
         const int32_t row = __ldg(v.nbr + brick * (uint32_t)Q + (lane < (uint32_t)Q ? lane : 0u));
-        if constexpr (HRAW) {
-            uint16_t h[Q];
-            fetch_ab_shfl_raw(src, n, row, slot, wm, fluid, h);
-            if (!fluid) return;
-            if (plain) {
-                collide_fast_finish<Lane1, true>(d, raw_moments_h1<ST>(h), la.s2, la.g);
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = w_of(i) * Mixed<ST>::cvt(h[i]);
-                wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
-                collide_model<COLL, X>(d, la);
-            }
-        } else {
-            fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
-            if (!fluid) return;
-            if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
-            collide_model<COLL, X>(d, la);
-        }
+        fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
+        if (!fluid) return;
+        if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
+        collide_model<COLL, X>(d, la);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if (!LBM_IN_RANGE((uint32_t)i * n + slot, (uint64_t)Q * n, 4)) continue;
@@ -1034,48 +831,18 @@ __global__ void __launch_bounds__(BRICKS * 32, MINB)
     const bool clean = PC >= 0 && __all_sync(0xffffffffu, ((wA | wB) & WORD_WALL_MASK) == 0u);
     if (!fA && !fB) return;
     float dA[Q], dB[Q];
+    if (fA) fetch_et<ST, true, PC>(pop, n, csA, wA & WORD_WALL_MASK, a.parity, dA, clean);
+    if (fB) fetch_et<ST, true, PC>(pop, n, csB, wB & WORD_WALL_MASK, a.parity, dB, clean);
+    const uint32_t halfA =
+        (fA && (wA & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotA, wA, a, dA) : 0u;
+    const uint32_t halfB =
+        (fB && (wB & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotB, wB, a, dB) : 0u;
     const float s2A = (wA & WORD_OWN_TAU) ? __ldg(v.s2_cell + slotA) : a.s2;
     const float s2B = (wB & WORD_OWN_TAU) ? __ldg(v.s2_cell + slotB) : a.s2;
     float2 d2[Q];
-    uint32_t halfA = 0u, halfB = 0u;
-    if constexpr (ST == LBM_STORE_FP32) {
-        if (fA) fetch_et<ST, true, PC>(pop, n, csA, wA & WORD_WALL_MASK, a.parity, dA, clean);
-        if (fB) fetch_et<ST, true, PC>(pop, n, csB, wB & WORD_WALL_MASK, a.parity, dB, clean);
-        halfA = (fA && (wA & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotA, wA, a, dA) : 0u;
-        halfB = (fB && (wB & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotB, wB, a, dB) : 0u;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d2[i] = make_float2(fA ? dA[i] : 0.0f, fB ? dB[i] : 0.0f);  // a solid lane: rest
-        collide_fast_t<Lane2, true>(d2, make_float2(s2A, s2B), a.g);  // stores through Store::store_x
-    } else {
-        // 16-bit storage: each cell's raw moments as in the one-cell kernel (from h for a plain
-        // cell, from d after its rules otherwise), then the rest of both collisions packed
-        auto cell_moments = [&](bool f, uint32_t w, uint32_t slot, const uint32_t (&cs)[8], float (&d)[Q],
-                                uint32_t& half) {
-            RawMoments<Lane1> m{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // a solid lane: rest
-            if (!f) return m;
-            uint16_t h[Q];
-            fetch_et_raw<true, PC>(pop, n, cs, w & WORD_WALL_MASK, a.parity, h, clean);
-            if (((w >> WORD_KIND_SHIFT) & 3u) == KIND_PLAIN) return raw_moments_h1<ST>(h);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) d[i] = w_of(i) * Mixed<ST>::cvt(h[i]);
-            half = wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slot, w, a, d);
-            return raw_moments_d<Lane1>(d);
-        };
-        const RawMoments<Lane1> mA = cell_moments(fA, wA, slotA, csA, dA, halfA);
-        const RawMoments<Lane1> mB = cell_moments(fB, wB, slotB, csB, dB, halfB);
-        RawMoments<Lane2> m2;
-        m2.drho = make_float2(mA.drho, mB.drho);
-        m2.jx = make_float2(mA.jx, mB.jx);
-        m2.jy = make_float2(mA.jy, mB.jy);
-        m2.jz = make_float2(mA.jz, mB.jz);
-        m2.Pxx = make_float2(mA.Pxx, mB.Pxx);
-        m2.Pyy = make_float2(mA.Pyy, mB.Pyy);
-        m2.Pzz = make_float2(mA.Pzz, mB.Pzz);
-        m2.Pxy = make_float2(mA.Pxy, mB.Pxy);
-        m2.Pxz = make_float2(mA.Pxz, mB.Pxz);
-        m2.Pyz = make_float2(mA.Pyz, mB.Pyz);
-        collide_fast_finish<Lane2, true>(d2, m2, make_float2(s2A, s2B), a.g);
-    }
+    for (int i = 0; i < Q; ++i) d2[i] = make_float2(fA ? dA[i] : 0.0f, fB ? dB[i] : 0.0f);  // a solid lane: rest
+    collide_fast_t<Lane2, true>(d2, make_float2(s2A, s2B), a.g);  // stores through Store::store_x
     if (fA) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) dA[i] = d2[i].x;
@@ -1241,12 +1008,21 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int targ
 template <int ST, int BRICKS, int MINB, int COLL, int P0>
 __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
     k_step_batch_persistent(const BatchEntry* __restrict__ ent, const int64_t* __restrict__ brick_start, int n_dom,
-                            const LevelArgs* __restrict__ args, int steps, GridBarrier* bar, uint64_t limit_ns)
+                            const LevelArgs* __restrict__ args, int steps, GridBarrier* bar, unsigned int* tickets,
+                            uint64_t limit_ns)
 {
     const int64_t total = __ldg(brick_start + n_dom);
     const int64_t n_units = (total + BRICKS - 1) / BRICKS;
+    __shared__ unsigned int next;
     for (int s = 0; s < steps; ++s) {
-        for (int64_t unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+        // units of step s are handed out by a ticket counter (tickets[s], cleared before the
+        // launch), so that CTAs that finish early take more
+        for (;;) {
+            __syncthreads();  // every thread has read the previous ticket
+            if (threadIdx.x == 0) next = atomicAdd(&tickets[s], 1u);
+            __syncthreads();
+            const int64_t unit = next;
+            if (unit >= n_units) break;
             const int64_t gbrick = unit * BRICKS + (threadIdx.x / BRICK_CELLS);
             if (gbrick < total) {  // whole warps
                 int lo = 0, hi = n_dom - 1;
@@ -1719,13 +1495,15 @@ cudaError_t launch_step_batch_t(const BatchEntry* ent, const int64_t* brick_star
     });
 }
 
-// one cooperative launch of k_step_batch_persistent (128 threads, 6 CTAs per SM at most): as many
-// CTAs as can be resident, never more than units of work
+// one cooperative launch of k_step_batch_persistent (128 threads, 8 CTAs per SM at most): as many
+// CTAs as can be resident, never more than units of work; bar is followed by `steps` ticket
+// counters, all cleared before the launch
 template <int ST, int COLL, int P0>
 cudaError_t launch_persistent_t(const BatchEntry* ent, const int64_t* brick_start, int n_dom, int64_t total_bricks,
                                 const LevelArgs* args, int steps, GridBarrier* bar, uint64_t limit_ns, cudaStream_t s)
 {
-    constexpr int BRICKS = 2, MINB = 6;
+    constexpr int BRICKS = 2, MINB = 8;
+    unsigned int* tickets = reinterpret_cast<unsigned int*>(bar + 1);  // [steps] after the barrier word
     auto k = k_step_batch_persistent<ST, BRICKS, MINB, COLL, P0>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1735,7 +1513,7 @@ cudaError_t launch_persistent_t(const BatchEntry* ent, const int64_t* brick_star
     const int64_t units = (total_bricks + BRICKS - 1) / BRICKS;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)sms * per_sm));
     void* kargs[] = {(void*)&ent, (void*)&brick_start, (void*)&n_dom, (void*)&args, (void*)&steps, (void*)&bar,
-                     (void*)&limit_ns};
+                     (void*)&tickets, (void*)&limit_ns};
     return cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(BRICKS * BRICK_CELLS), kargs, 0, s);
 }
 

@@ -1229,7 +1229,9 @@ struct lbm_batch {
                                         stream);
         const Launchers& L = launchers(storage);
         if (persistent) {
-            if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, sizeof(GridBarrier), stream);
+            // the barrier word and the per-step ticket counters that follow it
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(d_bar, 0, sizeof(GridBarrier) + sizeof(unsigned int) * (size_t)steps, stream);
             if (e == cudaSuccess)
                 e = L.step_batch_persistent(d_ent, d_start, n(), total_bricks, d_args, coll, common_parity(0), steps,
                                             d_bar, limit_ns, stream);
@@ -1326,7 +1328,8 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, int32_t graph_st
         B->d_ent = static_cast<BatchEntry*>(B->owner->dev_alloc(sizeof(BatchEntry) * (size_t)n));
         B->d_start = static_cast<int64_t*>(B->owner->dev_alloc(sizeof(int64_t) * ((size_t)n + 1)));
         B->d_args = static_cast<LevelArgs*>(B->owner->dev_alloc(B->args_bytes));
-        B->d_bar = static_cast<GridBarrier*>(B->owner->dev_alloc(sizeof(GridBarrier)));
+        B->d_bar = static_cast<GridBarrier*>(
+            B->owner->dev_alloc(sizeof(GridBarrier) + sizeof(unsigned int) * (size_t)graph_steps));
         if (!B->d_ent || !B->d_start || !B->d_args || !B->d_bar) st = fail(LBM_ERR_OOM, "allocation failed: batch tables");
     }
     if (!st) {

@@ -52,12 +52,16 @@ def test_periodic_pipe_split_along_its_axis(n_parts):
     assert np.abs(u[2]).max() > 1e-4
 
 
-@pytest.mark.parametrize("n_parts,storage", [(2, "fp32"), (3, "fp32"), (2, "fp16")])
-def test_aneurysm_split(n_parts, storage):
+@pytest.mark.parametrize("n_parts,storage,axis", [(2, "fp32", None), (3, "fp32", 0), (3, "fp32", 1), (2, "fp16", None)])
+def test_aneurysm_split(n_parts, storage, axis):
     """The 64^3 synthetic aneurysm (Bouzidi walls, pulsatile inlet, outlet, absorbing layer),
-    split along z: cuts through the vessel, the sac and the relaxation-time field."""
+    split along z (two slabs: the cut goes through the vessel, the sac and the relaxation-time
+    field), along x (three slabs: cuts through the outlet segment and the sac) and along y
+    (three slabs: through the inlet segment)."""
     g = I.aneurysm(2, edge=64, period=200.0, reynolds=30.0)
-    _compare(g, n_parts, 150, storage=storage)
+    plan = S.SlabPlan(g.mask.shape, g.periodic, n_parts, axis)
+    assert len(plan.transfers(g.mask)) >= 2  # every case exchanges across at least one cut
+    _compare(g, n_parts, 150, storage=storage, axis=axis)
 
 
 def test_split_across_the_inlet_face():
