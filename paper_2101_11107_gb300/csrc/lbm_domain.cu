@@ -482,6 +482,10 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
             const int layer = side ? n3[a] - 1 : 0, inner = side ? n3[a] - 2 : 1;
             std::vector<int32_t> hs((size_t)area, -1), is((size_t)area, -1);
             bool any = false;
+            // the halo layer and the layer inside it are independent: the neighbour's halo
+            // holds a copy of the whole inner layer, wherever that layer is fluid, whatever
+            // this side's halo holds at the same position (the two cross-sections differ
+            // wherever a cut crosses a curved vessel)
             for (int v = 0; v < n3[c]; ++v)
                 for (int u = 0; u < n3[b]; ++u) {
                     int p[3];
@@ -489,9 +493,10 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
                     p[b] = u;
                     p[c] = v;
                     const int64_t bi = p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2]);
-                    if (mask[bi] != 4) continue;
-                    any = true;
-                    hs[(size_t)(u + (int64_t)n3[b] * v)] = (int32_t)slot_of(p[0], p[1], p[2]);
+                    if (mask[bi] == 4) {
+                        any = true;
+                        hs[(size_t)(u + (int64_t)n3[b] * v)] = (int32_t)slot_of(p[0], p[1], p[2]);
+                    }
                     if (n3[a] < 2) continue;
                     p[a] = inner;
                     const int64_t ii = p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2]);
