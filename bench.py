@@ -474,7 +474,9 @@ def main():
                              "roofline_larger_than_l2"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nbox, "d2h_bytes_per_step": 16 * nbox,
-                "inner_lbm_steps": inner},
+                "inner_lbm_steps": inner,
+                "note": "per e2e step: upload of rho, u from pinned host memory, 200 lattice steps back to back "
+                        "(no L2 flush between them, unlike the device-timed value), read-back of rho, u"},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "variants": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in r.items()}

@@ -84,7 +84,8 @@ typedef struct {
     double force_amp[3]; /* g(n) = force + force_amp cos(force_omega n) */
     double force_omega;  /* angular frequency per step of the body-force modulation */
     double rho_out;      /* density imposed at outlet cells; default 1 */
-    int32_t periodic[3]; /* nonzero: the axis wraps (its extent must be a multiple of 4) */
+    int32_t periodic[3]; /* nonzero: the axis wraps (its extent must be a multiple of the brick's
+                            extent along it: 4 in the default build) */
     int32_t storage;     /* lbm_storage */
     int32_t scheme;      /* lbm_scheme; default ESOTERIC */
     int32_t collision;   /* lbm_collision; default CHM_MRT */
@@ -99,7 +100,7 @@ typedef void (*lbm_free_fn)(void* ptr, void* ctx);
 typedef struct {
     int32_t nx, ny, nz;
     int64_t n_fluid;         /* cells updated per step (mask 1, 2 or 3) */
-    int64_t n_bricks;        /* 4x4x4 bricks holding at least one fluid or halo cell */
+    int64_t n_bricks;        /* bricks (64 cells) holding at least one fluid or halo cell */
     int64_t n_slots;         /* 64 * n_bricks: population slots per direction */
     int64_t n_wall_cells;    /* fluid cells with at least one wall link */
     int64_t n_bouzidi_cells; /* fluid cells with at least one Bouzidi link */

@@ -18,6 +18,10 @@ LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
 # accesses skipped and reported as LBM_ERR_STATE at the next synchronising call
 DEBUG_OUT_DIR = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(DEBUG_OUT_DIR, "liblbm_gb300_debug.so")
+# a variant with 8 x 4 x 2 bricks in place of 4 x 4 x 4 (periodic extents: multiples of 8, 4, 2)
+B842_OUT_DIR = os.path.join(HERE, "_build_b842")
+B842_LIB = os.path.join(B842_OUT_DIR, "liblbm_gb300_b842.so")
+B842_FLAGS = ("-DLBM_BRICK_X=8", "-DLBM_BRICK_Y=4", "-DLBM_BRICK_Z=2")
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -41,12 +45,14 @@ def up_to_date(lib: str = LIB) -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
-    """Builds the library (debug: the LBM_DEBUG variant in its own folder) unless it is newer
-    than every source; returns its path."""
-    out_dir, lib = (DEBUG_OUT_DIR, DEBUG_LIB) if debug else (OUT_DIR, LIB)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False, brick842: bool = False) -> str:
+    """Builds the library (debug: the LBM_DEBUG variant; brick842: the 8 x 4 x 2 brick variant;
+    each in its own folder) unless it is newer than every source; returns its path."""
+    out_dir, lib = (DEBUG_OUT_DIR, DEBUG_LIB) if debug else (B842_OUT_DIR, B842_LIB) if brick842 else (OUT_DIR, LIB)
     if debug:
         extra_flags = ("-DLBM_DEBUG", *extra_flags)
+    if brick842:
+        extra_flags = (*B842_FLAGS, *extra_flags)
     if not force and up_to_date(lib):
         return lib
     os.makedirs(out_dir, exist_ok=True)
@@ -70,4 +76,5 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: boo
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv,
+                brick842="--brick842" in sys.argv,
                 extra_flags=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else []))

@@ -152,14 +152,14 @@ __device__ __forceinline__ void fetch_ab(const void* __restrict__ src, uint32_t 
                                          uint32_t slot, uint32_t wm, float (&d)[Q])
 {
     const int l = (int)(slot & (BRICK_CELLS - 1));
-    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+    const int lx = l & (BX - 1), ly = (l >> LBX) & (BY - 1), lz = l >> (LBX + LBY);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
-        // sx in [-1, 4]: the arithmetic shift gives the brick offset -1, 0 or +1
-        const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+        // sx in [-1, BX]: the arithmetic shift gives the brick offset -1, 0 or +1
+        const int ob = 13 + (sx >> LBX) + 3 * (sy >> LBY) + 9 * (sz >> LBZ);
         const uint32_t nb = (uint32_t)nbrow[ob];
-        const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
+        const uint32_t s = nb * BRICK_CELLS + (uint32_t)brick_local(sx & (BX - 1), sy & (BY - 1), sz & (BZ - 1));
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
         d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load(src, i, off) : 0.0f;
@@ -174,13 +174,13 @@ __device__ __forceinline__ void fetch_ab_shfl(const void* __restrict__ src, uint
                                               uint32_t slot, uint32_t wm, bool fluid, float (&d)[Q])
 {
     const int l = (int)(slot & (BRICK_CELLS - 1));
-    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+    const int lx = l & (BX - 1), ly = (l >> LBX) & (BY - 1), lz = l >> (LBX + LBY);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int sx = lx - cx_of(i), sy = ly - cy_of(i), sz = lz - cz_of(i);
-        const int ob = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+        const int ob = 13 + (sx >> LBX) + 3 * (sy >> LBY) + 9 * (sz >> LBZ);
         const uint32_t nb = (uint32_t)__shfl_sync(0xffffffffu, row_lane, ob);
-        const uint32_t s = nb * BRICK_CELLS + (uint32_t)((sx & 3) + ((sy & 3) << 2) + ((sz & 3) << 4));
+        const uint32_t s = nb * BRICK_CELLS + (uint32_t)brick_local(sx & (BX - 1), sy & (BY - 1), sz & (BZ - 1));
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
         if (fluid) d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load(src, i, off) : 0.0f;
@@ -191,13 +191,13 @@ __device__ __forceinline__ void fetch_ab_shfl(const void* __restrict__ src, uint
 __device__ __forceinline__ void corner_slots_shfl(int32_t row_lane, uint32_t slot, uint32_t (&cs)[8])
 {
     const int l = (int)(slot & (BRICK_CELLS - 1));
-    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+    const int lx = l & (BX - 1), ly = (l >> LBX) & (BY - 1), lz = l >> (LBX + LBY);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int tx = lx + (e & 1), ty = ly + ((e >> 1) & 1), tz = lz + (e >> 2);
-        const int ob = (tx >> 2) | ((ty >> 2) << 1) | ((tz >> 2) << 2);
+        const int ob = (tx >> LBX) | ((ty >> LBY) << 1) | ((tz >> LBZ) << 2);
         const uint32_t nb = (uint32_t)__shfl_sync(0xffffffffu, row_lane, ob);
-        cs[e] = nb * BRICK_CELLS + (uint32_t)((tx & 3) + ((ty & 3) << 2) + ((tz & 3) << 4));
+        cs[e] = nb * BRICK_CELLS + (uint32_t)brick_local(tx & (BX - 1), ty & (BY - 1), tz & (BZ - 1));
     }
 }
 
@@ -205,12 +205,12 @@ __device__ __forceinline__ void corner_slots_shfl(int32_t row_lane, uint32_t slo
 __device__ __forceinline__ void corner_slots(const int32_t* nb8, uint32_t slot, uint32_t (&cs)[8])
 {
     const int l = (int)(slot & (BRICK_CELLS - 1));
-    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
+    const int lx = l & (BX - 1), ly = (l >> LBX) & (BY - 1), lz = l >> (LBX + LBY);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int tx = lx + (e & 1), ty = ly + ((e >> 1) & 1), tz = lz + (e >> 2);
-        const int ob = (tx >> 2) | ((ty >> 2) << 1) | ((tz >> 2) << 2);
-        cs[e] = (uint32_t)nb8[ob] * BRICK_CELLS + (uint32_t)((tx & 3) + ((ty & 3) << 2) + ((tz & 3) << 4));
+        const int ob = (tx >> LBX) | ((ty >> LBY) << 1) | ((tz >> LBZ) << 2);
+        cs[e] = (uint32_t)nb8[ob] * BRICK_CELLS + (uint32_t)brick_local(tx & (BX - 1), ty & (BY - 1), tz & (BZ - 1));
     }
 }
 
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(BRICKS * BRICK_CELLS, MINB)
 }
 
 // Esoteric-twist step with two cells per thread: lane l of a warp updates cells l and l + 32 of
-// one brick (its lz = 0-1 and lz = 2-3 halves), and their collisions run as one stream of packed
+// one brick (its lower and upper halves along z), and their collisions run as one stream of packed
 // FP32x2 instructions (the default rates only), which halves the issue slots of the arithmetic;
 // loads, wall rules and stores stay per cell.  A warp covers one brick, so the brick's corner
 // row still goes round by shuffle.  Results are bit-identical to the one-cell kernels.

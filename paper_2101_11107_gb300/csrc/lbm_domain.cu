@@ -246,12 +246,13 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
     const int n3[3] = {nx, ny, nz};
     for (int d = 0; d < 3; ++d) {
         P.periodic[d] = P.periodic[d] ? 1 : 0;
-        if (P.periodic[d] && n3[d] % BRICK_EDGE != 0)
-            return fail(LBM_ERR_INVALID_ARG, "a periodic axis must have an extent that is a multiple of 4");
+        if (P.periodic[d] && n3[d] % BRICK_EXT[d] != 0)
+            return fail(LBM_ERR_INVALID_ARG, "a periodic axis must have an extent that is a multiple of the brick's ("
+                                                 + std::to_string(BRICK_EXT[d]) + ")");
     }
 
     // ---------------------------------------------------------------- bricks
-    const int nbx = (nx + 3) / 4, nby = (ny + 3) / 4, nbz = (nz + 3) / 4;
+    const int nbx = (nx + BX - 1) / BX, nby = (ny + BY - 1) / BY, nbz = (nz + BZ - 1) / BZ;
     const int64_t n_brick_box = (int64_t)nbx * nby * nbz;
     std::vector<int32_t> brick_id((size_t)n_brick_box, -1);
     int64_t n_fluid = 0, n_halo = 0;
@@ -278,7 +279,7 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
                 if (mask[x + (int64_t)nx * (y + (int64_t)ny * z)])
-                    brick_id[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nby * (z >> 2))] = 0;
+                    brick_id[(x >> LBX) + (int64_t)nbx * ((y >> LBY) + (int64_t)nby * (z >> LBZ))] = 0;
     // active bricks (holding fluid) are numbered first, in box order; then, for the esoteric
     // twist, every brick at an offset in {0,1}^3 of an active one (storage for the links of the
     // update's 8-cell corner), on a brick grid extended by one along non-periodic axes
@@ -336,8 +337,8 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
             }
     }
     auto slot_of = [&](int x, int y, int z) -> int64_t {
-        const int64_t b = brick_id[(x >> 2) + (int64_t)nbx * ((y >> 2) + (int64_t)nby * (z >> 2))];
-        return b * BRICK_CELLS + (x & 3) + ((y & 3) << 2) + ((z & 3) << 4);
+        const int64_t b = brick_id[(x >> LBX) + (int64_t)nbx * ((y >> LBY) + (int64_t)nby * (z >> LBZ))];
+        return b * BRICK_CELLS + brick_local(x & (BX - 1), y & (BY - 1), z & (BZ - 1));
     };
     // fluid index of the box cell shifted by s * c_i, or -1 (solid / outside a non-periodic face)
     auto shifted_fluid = [&](int x, int y, int z, int i, int s) -> int64_t {

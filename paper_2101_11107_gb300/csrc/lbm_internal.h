@@ -39,11 +39,25 @@ __host__ __device__ constexpr float pow2_neg(int k) { return k == 0 ? 1.0f : k =
 __host__ __device__ constexpr int corner_pos(int i) { return (cx_of(i) > 0) + 2 * (cy_of(i) > 0) + 4 * (cz_of(i) > 0); }
 __host__ __device__ constexpr int corner_neg(int i) { return (cx_of(i) < 0) + 2 * (cy_of(i) < 0) + 4 * (cz_of(i) < 0); }
 
-// Geometry is stored in 4x4x4 bricks; a population slot is brick * 64 + lx + 4 ly + 16 lz.
+// Geometry is stored in bricks of BX x BY x BZ = 64 cells (powers of two; 4 x 4 x 4 unless the
+// library is built with LBM_BRICK_X/Y/Z); a population slot is brick * 64 + lx + BX (ly + BY lz).
 // Bricks holding fluid ("active", updated every step) come first; the esoteric-twist layout adds
-// the bricks at offsets {0,1}^3 of active bricks ("halo", storage only).
-constexpr int BRICK_EDGE = 4;
+// the bricks at offsets {0,1}^3 of active bricks ("halo", storage only).  A warp covers half a
+// brick (lz < BZ / 2 or lz >= BZ / 2).
+#ifndef LBM_BRICK_X
+#define LBM_BRICK_X 4
+#define LBM_BRICK_Y 4
+#define LBM_BRICK_Z 4
+#endif
+constexpr int BX = LBM_BRICK_X, BY = LBM_BRICK_Y, BZ = LBM_BRICK_Z;
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+constexpr int LBX = ilog2(BX), LBY = ilog2(BY), LBZ = ilog2(BZ);
 constexpr int BRICK_CELLS = 64;
+static_assert(BX * BY * BZ == BRICK_CELLS && (1 << LBX) == BX && (1 << LBY) == BY && (1 << LBZ) == BZ && BZ >= 2,
+              "a brick is 64 cells, each extent a power of two, at least two layers along z");
+constexpr int BRICK_EXT[3] = {BX, BY, BZ};
+// local index of (lx, ly, lz) in a brick; (lx, ly, lz) of a local index
+__host__ __device__ constexpr int brick_local(int lx, int ly, int lz) { return lx | (ly << LBX) | (lz << (LBX + LBY)); }
 
 // Per-slot cell word (active bricks).
 //   bits 0..26  wall mask: bit i set <=> the pull source x - c_i is not a fluid cell
