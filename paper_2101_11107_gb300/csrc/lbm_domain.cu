@@ -914,6 +914,20 @@ lbm_status lbm_probe(lbm_domain* D, const int64_t* fluid_index, int32_t n, float
     return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace lbm {
+cudaError_t enqueue_velocity_correction(lbm_domain* D, const float* rho, const float* u, const float* du)
+{
+    const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
+    return launchers(D->params.storage)
+        .apply_du(D->params.scheme, D->view, D->src(), (int)((D->time + 1) & 1), D->d_fl_slot, D->d_fl_box,
+                  D->n_fluid, rho, u, du, n_box, D->stream);
+}
+}  // namespace lbm
+
+extern "C" {
+
 lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t device_ptrs)
 {
     NvtxRange nvtx_range("lbm_apply_velocity_correction");
@@ -940,9 +954,7 @@ lbm_status lbm_apply_velocity_correction(lbm_domain* D, const float* du, int32_t
     if (e == cudaSuccess)
         e = L.macroscopic(D->params.scheme, D->view, D->src(), a, D->d_fl_slot, D->d_fl_box, D->n_fluid, 1, rho, u,
                           n_box, D->stream);
-    if (e == cudaSuccess)
-        e = L.apply_du(D->params.scheme, D->view, D->src(), (int)((D->time + 1) & 1), D->d_fl_slot, D->d_fl_box,
-                       D->n_fluid, rho, u, dd, n_box, D->stream);
+    if (e == cudaSuccess) e = enqueue_velocity_correction(D, rho, u, dd);
     if (!device_ptrs) {  // the host array may be reused as soon as the call returns
         cudaError_t e2 = cudaStreamSynchronize(D->stream);
         if (e == cudaSuccess) e = e2;

@@ -198,6 +198,10 @@ struct DomainAccess {
     cudaStream_t stream;
 };
 bool domain_access(const lbm_domain* dom, DomainAccess* out);
+// the velocity correction of lbm_apply_velocity_correction with the current level's rho and u
+// already exported (dense device arrays, as lbm_get_macroscopic writes them): enqueued on the
+// domain's stream
+cudaError_t enqueue_velocity_correction(lbm_domain* dom, const float* rho, const float* u, const float* du);
 // sets the calling thread's lbm_last_error() message
 void set_last_error(const char* msg);
 

@@ -951,8 +951,10 @@ lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t*
         e = cudaEventRecord(K->ev, K->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(da.stream, K->ev, 0);
     }
+    // the correction reuses the rho, u exported above (the domain has not stepped since)
+    if (e == cudaSuccess) e = enqueue_velocity_correction(dom, K->rho, K->u, K->du);
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector apply: ") + cudaGetErrorString(e));
-    return lbm_apply_velocity_correction(dom, K->du, 1);
+    return LBM_OK;
 }
 
 void lbm_corrector_destroy(lbm_corrector* K)

@@ -5,7 +5,10 @@
     python -m paper_2101_11107_gb300.run_case corrector128 fp32 50
 
 Workloads: womersley (64x64x256 pulsatile pipe, radius 28), poiseuille (32x32x64 pipe,
-radius 12), aneurysm256 / aneurysm512 (seeded synthetic aneurysm, seed 11); corrector<edge>: the
+radius 12), aneurysm256 / aneurysm512 (seeded synthetic aneurysm, seed 11); batch16: the 16
+seeded aneurysms of the benchmark's batched variant (edges 96-192), advanced `steps` steps by one
+batched launch per step (graph chunks of 10; launch config name as the last argument, or
+"persistent"); corrector<edge>: the
 learned corrector's forward pass (features, three convolutions, output) on the seed-200
 synthetic aneurysm at that edge after 100 solver steps, repeated `steps` times (initial
 parameters of seed 0), with its CUDA-event time per pass.
@@ -44,6 +47,23 @@ def main(argv=None):
         e1.record()
         torch.cuda.synchronize()
         print(f"ok {case} fluid={g.nfluid} forward_ms={e0.elapsed_time(e1) / max(steps, 1):.4f}")
+        return
+    if case == "batch16":
+        import numpy as np
+
+        rng = np.random.default_rng(2024)
+        edges = [int(96 + 16 * rng.integers(0, 7)) for _ in range(16)]
+        doms = [lbm.Domain.from_geometry(I.aneurysm(300 + k, edge=e, wave_seed=400 + k), storage=storage)
+                for k, e in enumerate(edges)]
+        batch = lbm.Batch(doms, graph_steps=10)
+        if config == "persistent":
+            batch.set_persistent(True, 1.0)
+        elif config is not None:
+            batch.set_launch_config(lbm.LAUNCH_CONFIG_NAMES.index(config))
+        batch.step(steps)
+        batch.sync()
+        print(f"ok batch16 {storage} steps={steps} fluid={batch.n_fluid} config={config}")
+        batch.close()
         return
     if case == "womersley":
         g = I.womersley_pipe()
