@@ -336,19 +336,9 @@ __device__ __forceinline__ uint32_t link_index(uint32_t off, uint32_t wm, int i)
     return off + (uint32_t)__popc(wm & ((1u << i) - 1u));
 }
 
-// the wall mask of a fluid Bouzidi cell, 0 for any other slot
-__device__ __forceinline__ uint32_t bouzidi_links(bool fluid, uint32_t word)
-{
-    return (fluid && ((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) ? (word & WORD_WALL_MASK) : 0u;
-}
-
-// `any_links` (warp-uniform where the caller can give it: the OR of the wall masks of the
-// warp's Bouzidi cells) lets a whole warp skip a direction in which none of its cells has a
-// link, instead of stepping every lane through all 27 predicated link bodies.
 template <int ST, int SCHEME>
 __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* src_ab, uint32_t slot,
-                                               uint32_t word, const LevelArgs& a, float (&d)[Q],
-                                               uint32_t any_links = WORD_WALL_MASK)
+                                               uint32_t word, const LevelArgs& a, float (&d)[Q])
 {
     const uint32_t wm = word & WORD_WALL_MASK;
     const int kind = (int)((word >> WORD_KIND_SHIFT) & 3u);
@@ -357,7 +347,6 @@ __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* 
         const uint32_t off = (uint32_t)v.aux[slot];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if (!(any_links & (1u << i))) continue;
             if (!(wm & (1u << i))) continue;
             const uint32_t li = link_index(off, wm, i);
             if (!LBM_IN_RANGE(li, v.n_bq, 5)) continue;
@@ -765,10 +754,9 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         uint32_t cs[8];
         corner_slots_shfl(row, slot, cs);
         const bool clean = PC >= 0 && __all_sync(0xffffffffu, wm == 0u);
-        const uint32_t links = __reduce_or_sync(0xffffffffu, bouzidi_links(fluid, word));
         if (!fluid) return;
         fetch_et<ST, true, PC>(dst, n, cs, wm, a.parity, d, clean);
-        const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d, links) : 0u;
+        const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d) : 0u;
         collide_model<COLL, X>(d, la);
         store_et<ST, PC, X>(dst, n, cs, a.parity, d);
         if (half) {
@@ -782,10 +770,9 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         }
     } else {
         const int32_t row = __ldg(v.nbr + brick * (uint32_t)Q + (lane < (uint32_t)Q ? lane : 0u));
-        const uint32_t links = __reduce_or_sync(0xffffffffu, bouzidi_links(fluid, word));
         fetch_ab_shfl<ST>(src, n, row, slot, wm, fluid, d);
         if (!fluid) return;
-        if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d, links);
+        if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d);
         collide_model<COLL, X>(d, la);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -842,15 +829,14 @@ __global__ void __launch_bounds__(BRICKS * 32, MINB)
     const uint32_t wA = __ldg(v.word + slotA), wB = __ldg(v.word + slotB);
     const bool fA = (wA & WORD_FLUID) != 0u, fB = (wB & WORD_FLUID) != 0u;
     const bool clean = PC >= 0 && __all_sync(0xffffffffu, ((wA | wB) & WORD_WALL_MASK) == 0u);
-    const uint32_t links = __reduce_or_sync(0xffffffffu, bouzidi_links(fA, wA) | bouzidi_links(fB, wB));
     if (!fA && !fB) return;
     float dA[Q], dB[Q];
     if (fA) fetch_et<ST, true, PC>(pop, n, csA, wA & WORD_WALL_MASK, a.parity, dA, clean);
     if (fB) fetch_et<ST, true, PC>(pop, n, csB, wB & WORD_WALL_MASK, a.parity, dB, clean);
     const uint32_t halfA =
-        (fA && (wA & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotA, wA, a, dA, links) : 0u;
+        (fA && (wA & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotA, wA, a, dA) : 0u;
     const uint32_t halfB =
-        (fB && (wB & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotB, wB, a, dB, links) : 0u;
+        (fB && (wB & WORD_WALL_MASK)) ? wall_rules<ST, LBM_SCHEME_ESOTERIC>(v, nullptr, slotB, wB, a, dB) : 0u;
     const float s2A = (wA & WORD_OWN_TAU) ? __ldg(v.s2_cell + slotA) : a.s2;
     const float s2B = (wB & WORD_OWN_TAU) ? __ldg(v.s2_cell + slotB) : a.s2;
     float2 d2[Q];
