@@ -307,18 +307,20 @@ def test_open_boundary_flux_diagnostics():
     assert d["flux_in"] > 0 and abs(d["flux_out"] / d["flux_in"] - 1.0) < 2e-2
 
 
-@pytest.mark.parametrize("scheme,k", [("esoteric", 51), ("esoteric", 50), ("ab", 51)])
-def test_checkpoint_round_trip(tmp_path, scheme, k):
+@pytest.mark.parametrize("scheme,k,storage", [("esoteric", 51, "fp32"), ("esoteric", 50, "fp32"), ("ab", 51, "fp32"),
+                                               ("esoteric", 51, "fp16"), ("ab", 50, "bf16")])
+def test_checkpoint_round_trip(tmp_path, scheme, k, storage):
     """N steps == k steps + save + load into a fresh domain + (N - k) steps, bit for bit
-    (odd and even k: the twist stores its populations by level parity)."""
+    (odd and even k: the twist stores its populations by level parity; 16-bit storage: the file
+    holds the stored 16-bit values)."""
     g = I.aneurysm(2, edge=64, period=200.0)
-    a = lbm.Domain.from_geometry(g, scheme=scheme)
+    a = lbm.Domain.from_geometry(g, scheme=scheme, storage=storage)
     a.step(120)
     rho_a, u_a = a.macroscopic()
-    b = lbm.Domain.from_geometry(g, scheme=scheme)
+    b = lbm.Domain.from_geometry(g, scheme=scheme, storage=storage)
     b.step(k)
     b.save_state(tmp_path / "ck.bin")
-    c = lbm.Domain.from_geometry(g, scheme=scheme)
+    c = lbm.Domain.from_geometry(g, scheme=scheme, storage=storage)
     c.load_state(tmp_path / "ck.bin")
     assert c.time == k
     c.step(120 - k)
@@ -585,3 +587,22 @@ def test_persistent_batch_barrier_gives_up():
         a.step(10)
         assert np.array_equal(d.macroscopic()[1], a.macroscopic()[1])
     b2.close()
+
+
+def test_checkpoint_refused_by_a_different_domain(tmp_path):
+    """A checkpoint loads only into a domain built from the same mask, links, storage and
+    scheme: another storage precision, another scheme or another geometry gives IO and leaves
+    the domain unchanged."""
+    g = I.aneurysm(2, edge=64, period=200.0)
+    a = lbm.Domain.from_geometry(g)
+    a.step(7)
+    a.save_state(tmp_path / "ck.bin")
+    for other in (lbm.Domain.from_geometry(g, storage="fp16"), lbm.Domain.from_geometry(g, scheme="ab"),
+                  lbm.Domain.from_geometry(I.aneurysm(3, edge=64, period=200.0))):
+        other.step(2)
+        before = other.macroscopic()
+        with pytest.raises(lbm.LbmError) as e:
+            other.load_state(tmp_path / "ck.bin")
+        assert e.value.status == 7 and other.time == 2
+        after = other.macroscopic()
+        assert np.array_equal(before[1], after[1])
