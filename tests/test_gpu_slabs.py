@@ -139,7 +139,7 @@ def test_two_processes_exchange_through_gloo():
     port = s.getsockname()[1]
     s.close()
     steps = 60
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.start_processes(_slab_rank, args=(2, port, steps, out), nprocs=2, start_method="spawn", join=True)
         res = dict(out)

@@ -141,7 +141,7 @@ def test_exchange_between_gloo_ranks(world, shape, periodic):
     packed on its opposite face: two ranks on a wrapped axis (both cuts between the same pair),
     two ranks on an open axis (one cut), three ranks on a wrapped axis."""
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.start_processes(_rank, args=(world, port, shape, periodic, out), nprocs=world, start_method="spawn",
                            join=True)
