@@ -621,10 +621,122 @@ __device__ __forceinline__ void collide_fast_t(typename L::V (&d)[Q], typename L
     for (int k = 0; k < 9; ++k) inv3_t<L, DEFER>(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, xc, x2);
 }
 
+// The fast collision of one cell with packed FP32x2 instructions inside the cell: the 1-D
+// sums along x and then y run on the z = -1 and z = +1 rows as pairs (their z = 0 rows alone),
+// and the inverse passes along z and then y on the x = -1 and x = +1 columns as pairs (x = 0
+// alone); the final pass along x mixes the members of a pair and stays scalar.  Every element
+// sees the operations of collide_fast_t<Lane1> in the same order, so results are bit-identical.
+template <bool DEFER = false>
+__device__ __forceinline__ void collide_fast_p(float (&d)[Q], float s2, const float g[3])
+{
+    using L = Lane1;
+    using P = Lane2;
+    // x sums of row k = q + 3 r; index q, .x the row at r = 0 (k = q), .y the row at r = 2 (k = q + 6)
+    float2 S0p[3], S1p[3], S2p[3];
+    float S0m[3], S1m[3], S2m[3];  // rows at r = 1 (k = q + 3)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int k0 = q, k2 = q + 6, k1 = q + 3;
+        const float2 gm = make_float2(d[3 * k0], d[3 * k2]), g0 = make_float2(d[3 * k0 + 1], d[3 * k2 + 1]),
+                     gp = make_float2(d[3 * k0 + 2], d[3 * k2 + 2]);
+        S2p[q] = P::add(gm, gp);
+        S0p[q] = P::add(S2p[q], g0);
+        S1p[q] = P::sub(gp, gm);
+        S2m[q] = L::add(d[3 * k1], d[3 * k1 + 2]);
+        S0m[q] = L::add(S2m[q], d[3 * k1 + 1]);
+        S1m[q] = L::sub(d[3 * k1 + 2], d[3 * k1]);
+    }
+    // y sums at z = -1 and z = +1 (pairs) and z = 0
+    const float2 T2p = P::add(S0p[0], S0p[2]);
+    const float2 T0p = P::add(T2p, S0p[1]);
+    const float2 T1p = P::sub(S0p[2], S0p[0]);
+    const float2 U0p = P::add(P::add(S1p[0], S1p[1]), S1p[2]);
+    const float2 U1p = P::sub(S1p[2], S1p[0]);
+    const float2 Wp = P::add(P::add(S2p[0], S2p[1]), S2p[2]);
+    const float T2m = L::add(S0m[0], S0m[2]);
+    const float T0m = L::add(T2m, S0m[1]);
+    const float T1m = L::sub(S0m[2], S0m[0]);
+    const float U0m = L::add(L::add(S1m[0], S1m[1]), S1m[2]);
+    const float U1m = L::sub(S1m[2], S1m[0]);
+    const float Wm = L::add(L::add(S2m[0], S2m[1]), S2m[2]);
+    const float T0[3] = {T0p.x, T0m, T0p.y}, T1[3] = {T1p.x, T1m, T1p.y}, T2[3] = {T2p.x, T2m, T2p.y};
+    const float U0[3] = {U0p.x, U0m, U0p.y}, U1[3] = {U1p.x, U1m, U1p.y}, W[3] = {Wp.x, Wm, Wp.y};
+    const float drho = L::add(L::add(T0[0], T0[1]), T0[2]);
+    const float jz = L::sub(T0[2], T0[0]);
+    const float Pzz = L::add(T0[2], T0[0]);
+    const float jy = L::add(L::add(T1[0], T1[1]), T1[2]);
+    const float Pyz = L::sub(T1[2], T1[0]);
+    const float Pyy = L::add(L::add(T2[0], T2[1]), T2[2]);
+    const float jx = L::add(L::add(U0[0], U0[1]), U0[2]);
+    const float Pxz = L::sub(U0[2], U0[0]);
+    const float Pxy = L::add(L::add(U1[0], U1[1]), U1[2]);
+    const float Pxx = L::add(L::add(W[0], W[1]), W[2]);
+    const float rho = L::one_plus(drho);
+    const float ir = L::rcp1p(drho);
+    const float ux = L::fma(jx, ir, 0.5f * g[0]);
+    const float uy = L::fma(jy, ir, 0.5f * g[1]);
+    const float uz = L::fma(jz, ir, 0.5f * g[2]);
+    const float ux2 = L::mul(ux, ux), uy2 = L::mul(uy, uy), uz2 = L::mul(uz, uz);
+    const float uxy = L::mul(ux, uy), uxz = L::mul(ux, uz), uyz = L::mul(uy, uz);
+    const float k2 = L::sub(1.0f, s2), ns2 = L::neg(s2);
+    const float mcs = -CS2;
+    const float a200 = L::fma(L::add(ux2, mcs), drho, L::fma(L::mul(-2.0f, ux), jx, Pxx));
+    const float a020 = L::fma(L::add(uy2, mcs), drho, L::fma(L::mul(-2.0f, uy), jy, Pyy));
+    const float a002 = L::fma(L::add(uz2, mcs), drho, L::fma(L::mul(-2.0f, uz), jz, Pzz));
+    const float a110 = L::fma(uxy, drho, L::fma(L::neg(ux), jy, L::fma(L::neg(uy), jx, Pxy)));
+    const float a101 = L::fma(uxz, drho, L::fma(L::neg(ux), jz, L::fma(L::neg(uz), jx, Pxz)));
+    const float a011 = L::fma(uyz, drho, L::fma(L::neg(uy), jz, L::fma(L::neg(uz), jy, Pyz)));
+    const float ex[3] = {1.0f, L::neg(ux), ux2}, ey[3] = {1.0f, L::neg(uy), uy2}, ez[3] = {1.0f, L::neg(uz), uz2};
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        const int p = m % 3, q = (m / 3) % 3, r = m / 9;
+        if (p + q + r < 3) continue;
+        float aw = ex[p];
+        if (q) aw = p ? L::mul(aw, ey[q]) : ey[q];
+        if (r) aw = (p || q) ? L::mul(aw, ez[r]) : ez[r];
+        d[m] = L::neg(aw);
+    }
+    d[0] = drho;
+    d[1] = L::fma(L::mul(0.5f, rho), g[0], ux);
+    d[3] = L::fma(L::mul(0.5f, rho), g[1], uy);
+    d[9] = L::fma(L::mul(0.5f, rho), g[2], uz);
+    d[2] = L::fma(k2, a200, L::mul(ns2, ux2));
+    d[6] = L::fma(k2, a020, L::mul(ns2, uy2));
+    d[18] = L::fma(k2, a002, L::mul(ns2, uz2));
+    d[4] = L::fma(k2, a110, L::mul(ns2, uxy));
+    d[10] = L::fma(k2, a101, L::mul(ns2, uxz));
+    d[12] = L::fma(k2, a011, L::mul(ns2, uyz));
+    const float zc = L::add(uz2, CS2), yc = L::add(uy2, CS2), xc = L::add(ux2, CS2);
+    const float z2 = L::mul(2.0f, uz), y2 = L::mul(2.0f, uy), x2 = L::mul(2.0f, ux);
+    // inverse along z: columns (p, q) with p = 0 and p = 2 as pairs
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float2 m0 = make_float2(d[3 * q], d[3 * q + 2]), m1 = make_float2(d[3 * q + 9], d[3 * q + 11]),
+               m2 = make_float2(d[3 * q + 18], d[3 * q + 20]);
+        inv3_t<P, DEFER>(m0, m1, m2, P::splat(uz), P::splat(zc), P::splat(z2));
+        d[3 * q] = m0.x, d[3 * q + 2] = m0.y, d[3 * q + 9] = m1.x, d[3 * q + 11] = m1.y;
+        d[3 * q + 18] = m2.x, d[3 * q + 20] = m2.y;
+        inv3_t<L, DEFER>(d[3 * q + 1], d[3 * q + 10], d[3 * q + 19], uz, zc, z2);
+    }
+    // inverse along y: columns (p, r), the same pairs
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float2 m0 = make_float2(d[9 * r], d[9 * r + 2]), m1 = make_float2(d[9 * r + 3], d[9 * r + 5]),
+               m2 = make_float2(d[9 * r + 6], d[9 * r + 8]);
+        inv3_t<P, DEFER>(m0, m1, m2, P::splat(uy), P::splat(yc), P::splat(y2));
+        d[9 * r] = m0.x, d[9 * r + 2] = m0.y, d[9 * r + 3] = m1.x, d[9 * r + 5] = m1.y;
+        d[9 * r + 6] = m2.x, d[9 * r + 8] = m2.y;
+        inv3_t<L, DEFER>(d[9 * r + 1], d[9 * r + 4], d[9 * r + 7], uy, yc, y2);
+    }
+    // inverse along x: rows, scalar
+#pragma unroll
+    for (int k = 0; k < 9; ++k) inv3_t<L, DEFER>(d[3 * k], d[3 * k + 1], d[3 * k + 2], ux, xc, x2);
+}
+
 template <bool DEFER = false>
 __device__ __forceinline__ void collide_fast(float (&d)[Q], const LevelArgs& a)
 {
-    collide_fast_t<Lane1, DEFER>(d, a.s2, a.g);
+    collide_fast_p<DEFER>(d, a.s2, a.g);
 }
 
 // The classical operators the paper compares against (Sec. 2.1.2), with the second-order
