@@ -74,10 +74,12 @@ struct Store;
 template <>
 struct Store<LBM_STORE_FP32> {
     using T = float;
+    static constexpr bool SCALED = false;  // the stored value is d itself
     static __device__ __forceinline__ float load(const void* p, int, uint32_t off)
     {
         return __ldg(static_cast<const float*>(p) + off);
     }
+    static __device__ __forceinline__ float load_h(const void* p, uint32_t off) { return load(p, 0, off); }
     // with a 256-byte L2 fetch on a miss: a warp reads 128 bytes of a brick's 256-byte plane
     // row and the other half-brick warp (or the neighbour brick's shifted read) the rest, so
     // the second request finds it in L2 (measured: -3% per step cold for the two-cell kernel,
@@ -90,10 +92,12 @@ struct Store<LBM_STORE_FP32> {
         asm("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(static_cast<const float*>(p) + off));
         return v;
     }
+    static __device__ __forceinline__ float load_rw_h(const void* p, uint32_t off) { return load_rw(p, 0, off); }
     static __device__ __forceinline__ void store(void* p, int, uint32_t off, float v)
     {
         static_cast<float*>(p)[off] = v;
     }
+    static __device__ __forceinline__ void store_h(void* p, uint32_t off, float v) { static_cast<float*>(p)[off] = v; }
     // v carries the factor 2^nnz(c_i) of the deferred-halving inverse transform (exact)
     static __device__ __forceinline__ void store_x(void* p, int i, uint32_t off, float v)
     {
@@ -111,6 +115,21 @@ struct Store<LBM_STORE_FP16> {
     static __device__ __forceinline__ float load_rw(const void* p, int i, uint32_t off)
     {
         return w_of(i) * __half2float(static_cast<const __half*>(p)[off]);
+    }
+    // the stored h = d / w as a float (the caller multiplies by w_i: scale_in)
+    static constexpr bool SCALED = true;
+    static __device__ __forceinline__ float load_h(const void* p, uint32_t off)
+    {
+        return __half2float(__ldg(static_cast<const __half*>(p) + off));
+    }
+    static __device__ __forceinline__ float load_rw_h(const void* p, uint32_t off)
+    {
+        return __half2float(static_cast<const __half*>(p)[off]);
+    }
+    // v already multiplied by the direction's store factor (scale_out)
+    static __device__ __forceinline__ void store_h(void* p, uint32_t off, float v)
+    {
+        static_cast<__half*>(p)[off] = __float2half_rn(v);
     }
     static __device__ __forceinline__ void store(void* p, int i, uint32_t off, float v)
     {
@@ -134,6 +153,21 @@ struct Store<LBM_STORE_BF16> {
     {
         return w_of(i) * __bfloat162float(static_cast<const __nv_bfloat16*>(p)[off]);
     }
+    // the stored h = d / w as a float (the caller multiplies by w_i: scale_in)
+    static constexpr bool SCALED = true;
+    static __device__ __forceinline__ float load_h(const void* p, uint32_t off)
+    {
+        return __bfloat162float(__ldg(static_cast<const __nv_bfloat16*>(p) + off));
+    }
+    static __device__ __forceinline__ float load_rw_h(const void* p, uint32_t off)
+    {
+        return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[off]);
+    }
+    // v already multiplied by the direction's store factor (scale_out)
+    static __device__ __forceinline__ void store_h(void* p, uint32_t off, float v)
+    {
+        static_cast<__nv_bfloat16*>(p)[off] = __float2bfloat16_rn(v);
+    }
     static __device__ __forceinline__ void store(void* p, int i, uint32_t off, float v)
     {
         static_cast<__nv_bfloat16*>(p)[off] = __float2bfloat16_rn(v * inv_w_of(i));
@@ -143,6 +177,57 @@ struct Store<LBM_STORE_BF16> {
         static_cast<__nv_bfloat16*>(p)[off] = __float2bfloat16_rn(v * (inv_w_of(i) * pow2_neg(nnz_of(i))));
     }
 };
+
+// The multiplies around the raw accessors, with packed FP32x2 instructions where two directions
+// share the factor (the same product as the per-direction load / store above, so bit-identical).
+// In: d_i = w_i h_i for the 16-bit storages; the directions j and j + 18 (c_z = -1 and +1, same
+// c_x, c_y) share w.
+template <int ST>
+__device__ __forceinline__ void scale_in(float (&d)[Q])
+{
+    if (!Store<ST>::SCALED) return;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const float2 v = __fmul2_rn(make_float2(d[j], d[j + 18]), make_float2(w_of(j), w_of(j)));
+        d[j] = v.x;
+        d[j + 18] = v.y;
+        d[j + 9] = d[j + 9] * w_of(j + 9);
+    }
+}
+
+// Out: the factor taking a post-collision d_i to the stored value -- 1/w_i for the 16-bit
+// storages, times 2^-nnz(c_i) when d carries the deferred-halving factors (X).
+template <int ST, bool X>
+__host__ __device__ constexpr float out_factor(int i)
+{
+    return (Store<ST>::SCALED ? inv_w_of(i) : 1.0f) * (X ? pow2_neg(nnz_of(i)) : 1.0f);
+}
+
+// the directions 3k and 3k + 2 (c_x = -1 and +1, same c_y, c_z) share the factor
+template <int ST, bool X>
+__device__ __forceinline__ void scale_out(float (&d)[Q])
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        constexpr float one = 1.0f;
+        if (out_factor<ST, X>(3 * k) != one) {
+            const float c = out_factor<ST, X>(3 * k);
+            const float2 v = __fmul2_rn(make_float2(d[3 * k], d[3 * k + 2]), make_float2(c, c));
+            d[3 * k] = v.x;
+            d[3 * k + 2] = v.y;
+        }
+        if (out_factor<ST, X>(3 * k + 1) != one) d[3 * k + 1] = d[3 * k + 1] * out_factor<ST, X>(3 * k + 1);
+    }
+}
+
+// two cells at once (a lane of the two-cell kernel): every direction one packed multiply
+template <int ST, bool X>
+__device__ __forceinline__ void scale_out2(float2 (&d)[Q])
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (out_factor<ST, X>(i) != 1.0f) d[i] = __fmul2_rn(d[i], make_float2(out_factor<ST, X>(i), out_factor<ST, X>(i)));
+}
 
 // ------------------------------------------------------------------------------ streaming
 // A-B pull: f_i(x, n) = f*_i(x - c_i, n - 1) from `src`; a wall link reads the cell's own
@@ -162,8 +247,9 @@ __device__ __forceinline__ void fetch_ab(const void* __restrict__ src, uint32_t 
         const uint32_t s = nb * BRICK_CELLS + (uint32_t)brick_local(sx & (BX - 1), sy & (BY - 1), sz & (BZ - 1));
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
-        d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load(src, i, off) : 0.0f;
+        d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load_h(src, off) : 0.0f;
     }
+    scale_in<ST>(d);
 }
 
 // A-B pull in the step kernel: the brick's 27-entry neighbour row is held by lanes 0..26 of the
@@ -183,8 +269,9 @@ __device__ __forceinline__ void fetch_ab_shfl(const void* __restrict__ src, uint
         const uint32_t s = nb * BRICK_CELLS + (uint32_t)brick_local(sx & (BX - 1), sy & (BY - 1), sz & (BZ - 1));
         const bool wall = (wm >> i) & 1u;
         const uint32_t off = wall ? (uint32_t)(Q - 1 - i) * n + slot : (uint32_t)i * n + s;
-        if (fluid) d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load(src, i, off) : 0.0f;
+        if (fluid) d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 1) ? Store<ST>::load_h(src, off) : 0.0f;
     }
+    if (fluid) scale_in<ST>(d);
 }
 
 // Twist corner slots in the step kernel: lanes hold the brick's nb8 row (lane & 7).
@@ -226,9 +313,10 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint32_t off = (PC ? (uint32_t)(Q - 1 - i) : (uint32_t)i) * n + cs[corner_neg(i)];
-            d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off))
+            d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? Store<ST>::load_rw_h(pop, off) : Store<ST>::load_h(pop, off))
                                                         : 0.0f;
         }
+        scale_in<ST>(d);
         return;
     }
     if (PC >= 0) parity = PC;
@@ -237,14 +325,16 @@ __device__ __forceinline__ void fetch_et(const void* pop, uint32_t n, const uint
         const uint32_t flip = ((uint32_t)parity ^ (wm >> i)) & 1u;
         const uint32_t dir = flip ? (uint32_t)(Q - 1 - i) : (uint32_t)i;
         const uint32_t off = dir * n + cs[corner_neg(i)];
-        d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? Store<ST>::load_rw(pop, i, off) : Store<ST>::load(pop, i, off))
+        d[i] = LBM_IN_RANGE(off, (uint64_t)Q * n, 2) ? (RW ? Store<ST>::load_rw_h(pop, off) : Store<ST>::load_h(pop, off))
                                                     : 0.0f;
     }
+    scale_in<ST>(d);
 }
 
 // Esoteric twist write after a step of parity P: f*_i to slot (P ? i : opp(i)) of cell x + p_i
-// (PC >= 0: the parity fixed at compile time; X: d carries the factors 2^nnz(c_i)).
-template <int ST, int PC = -1, bool X = false>
+// (PC >= 0: the parity fixed at compile time; X: d carries the factors 2^nnz(c_i); H: d has been
+// through scale_out, the stored values as floats).
+template <int ST, int PC = -1, bool X = false, bool H = false>
 __device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (&cs)[8], int parity,
                                          const float (&d)[Q])
 {
@@ -260,7 +350,8 @@ __device__ __forceinline__ void store_et(void* pop, uint32_t n, const uint32_t (
         const uint32_t dir = parity ? (uint32_t)i : (uint32_t)(Q - 1 - i);
         const uint32_t off = dir * n + cs[corner_pos(i)];
         if (!LBM_IN_RANGE(off, (uint64_t)Q * n, 3)) continue;
-        if (X) Store<ST>::store_x(pop, i, off, d[i]);
+        if (H) Store<ST>::store_h(pop, off, d[i]);
+        else if (X) Store<ST>::store_x(pop, i, off, d[i]);
         else Store<ST>::store(pop, i, off, d[i]);
     }
 }
@@ -874,15 +965,14 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         fetch_et<ST, true, PC>(dst, n, cs, wm, a.parity, d, clean);
         const uint32_t half = wm ? wall_rules<ST, SCHEME>(v, nullptr, slot, word, a, d, auxv) : 0u;
         collide_model<COLL, X>(d, la);
-        store_et<ST, PC, X>(dst, n, cs, a.parity, d);
+        scale_out<ST, X>(d);
+        store_et<ST, PC, X, true>(dst, n, cs, a.parity, d);
         if (half) {
             const uint32_t off = (uint32_t)auxv;
 #pragma unroll
             for (int i = 0; i < Q; ++i)
-                if ((half & (1u << i)) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5)) {
-                    if (X) Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
-                    else Store<ST>::store(v.side, i, link_index(off, wm, i), d[i]);
-                }
+                if ((half & (1u << i)) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5))
+                    Store<ST>::store_h(v.side, link_index(off, wm, i), d[i]);
         }
     } else {
         const int32_t row = __ldg(v.nbr + brick * (uint32_t)Q + (lane < (uint32_t)Q ? lane : 0u));
@@ -890,11 +980,11 @@ __device__ __forceinline__ void step_cell(const DomainView& v, const void* src, 
         if (!fluid) return;
         if (wm) wall_rules<ST, SCHEME>(v, src, slot, word, a, d, auxv);
         collide_model<COLL, X>(d, la);
+        scale_out<ST, X>(d);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if (!LBM_IN_RANGE((uint32_t)i * n + slot, (uint64_t)Q * n, 4)) continue;
-            if (X) Store<ST>::store_x(dst, i, (uint32_t)i * n + slot, d[i]);
-            else Store<ST>::store(dst, i, (uint32_t)i * n + slot, d[i]);
+            Store<ST>::store_h(dst, (uint32_t)i * n + slot, d[i]);
         }
     }
 }
@@ -919,14 +1009,14 @@ __device__ __forceinline__ void store_twist_cell(const DomainView& v, void* pop,
                                                  int32_t aux, const uint32_t (&cs)[8], uint32_t half,
                                                  const float (&d)[Q])
 {
-    store_et<ST, PC, true>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
+    store_et<ST, PC, true, true>(pop, (uint32_t)v.n_slots, cs, a.parity, d);
     if (half) {
         const uint32_t off = (uint32_t)aux;
         const uint32_t wm = word & WORD_WALL_MASK;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
             if ((half & (1u << i)) && LBM_IN_RANGE(link_index(off, wm, i), v.n_bq, 5))
-                Store<ST>::store_x(v.side, i, link_index(off, wm, i), d[i]);
+                Store<ST>::store_h(v.side, link_index(off, wm, i), d[i]);
     }
 }
 
@@ -960,7 +1050,8 @@ __global__ void __launch_bounds__(BRICKS * 32, MINB)
     float2 d2[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d2[i] = make_float2(fA ? dA[i] : 0.0f, fB ? dB[i] : 0.0f);  // a solid lane: rest
-    collide_fast_t<Lane2, true>(d2, make_float2(s2A, s2B), a.g);  // stores through Store::store_x
+    collide_fast_t<Lane2, true>(d2, make_float2(s2A, s2B), a.g);
+    scale_out2<ST, true>(d2);  // the store factors of both cells, one packed multiply per direction
     if (fA) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) dA[i] = d2[i].x;
