@@ -17,10 +17,10 @@
 //     with the accumulator in tensor memory, operands staged in shared memory by TMA, a CTA per
 //     8 x 16 x 1 slab (M = 128 cells, N = 16 output channels, K = 27 offsets x 16 input
 //     channels).  The data-gradient is the same kernel with the flipped, transposed kernel and
-//     a ReLU gate.  The weight-gradient is a GEMM over cells with M = 16 output channels, below
-//     the smallest tcgen05 tile (M = 64): it stays on warp-level mma.sync m16n8k16 (BF16 in,
-//     FP32 accumulate) with per-CTA register accumulation and one FP32 atomic per weight per
-//     CTA.
+//     a ReLU gate.  The weight-gradient is a GEMM over cells (K) whose M stacks the offsets along
+//     x with the input channels (k_wgrad_tc, also tcgen05): the three x-shifted copies of each
+//     halo row are transposed into shared memory so that every operand is a plain canonical
+//     layout, and the per-CTA partial sums are added in a fixed order.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -46,20 +46,6 @@ struct Box {
 __device__ __forceinline__ size_t pidx(const Box& b, int x, int y, int z)
 {
     return ((size_t)(z + 1) * b.py + (size_t)(y + 1)) * b.px + (size_t)(x + 1);
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
-{
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 // ------------------------------------------------------------------------------ tcgen05 conv
@@ -277,103 +263,233 @@ __global__ void __launch_bounds__(128)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase) : "memory");
 }
 
-// Partial weight gradient of this CTA's tiles: part[blockIdx.x] = (dW[o][co][ci] = sum_p dy[p][co]
-// x[p + o][ci], db[co] = sum_p dy[p][co]) over the tiles blockIdx.x, + gridDim.x, ...; each warp
-// owns offsets warp, warp + 4, ...  The partials are summed over the CTAs in a fixed order by
-// k_wgrad_reduce, so that a training run is reproducible bit for bit (float atomics would sum
-// them in whatever order the CTAs finish).
-constexpr int WG_CTAS = 304;  // weight-gradient CTAs (2 per SM): the partial buffer's depth
+// Partial weight gradient of this CTA's slabs on the 5th-generation tensor cores:
+// part[blockIdx.x] = (dW[o][co][ci] = sum_p dy[p][co] x[p + o][ci], db[co] = sum_p dy[p][co]) over
+// the cells p of slabs blockIdx.x, + gridDim.x, ...  The sums over the CTAs are taken in a fixed
+// order by k_wgrad_reduce, so that a training run is reproducible bit for bit.
+//   GEMM per pair (dy, dz) of offsets along y and z: D[(s, ci)][co] = sum_k A[(s, ci)][k] B[co][k]
+// with k running over the slab's cells (K = 16 per MMA: two x rows of 8 cells), A[(s, ci)][k] =
+// x[cell(k) + (s - 1, dy, dz)][ci] and B[co][k] = dy[cell(k)][co]; rows s = 0, 1, 2 are the three
+// offsets along x.  Both operands are K-major canonical layouts (8 x 16 B core matrices, no
+// swizzle) built in shared memory: for every halo row (y, z) the 8 cells that start at x0 - 1,
+// x0 and x0 + 1 are stored transposed, channel by channel ([ci][8 cells], 256 B each), one after
+// the other, so the M core matrices (s, ci / 8) of one offset pair lie 128 B apart and the next
+// 8 cells along K (the next x row) 768 B further.  An MMA has M = 128: rows s = 3..7 read the
+// following halo rows and are discarded.  The nine accumulators (16 columns each) stay in tensor
+// memory over all the CTA's slabs; two staging buffers let the threads transpose slab j + 1 while
+// the 72 MMAs of slab j run.  Every wait is bounded; on a timeout the CTA flags `err`, waits for
+// what it issued, frees its tensor memory and returns.
+constexpr int WG_CTAS = 304;                           // weight-gradient CTAs (2 per SM): the partial buffer's depth
+constexpr int WG_HROWS = HY * HZ;                      // 54 halo rows (y, z) of a slab
+constexpr uint32_t WG_ROW = 3 * 256;                   // one halo row: three shifted copies
+constexpr uint32_t WG_A = (WG_HROWS + 2) * WG_ROW;     // + 2 rows read only by the discarded M rows
+constexpr uint32_t WG_B = SL_Y * 256;                  // dy of the slab: 16 x rows of [co][8 cells]
+constexpr uint32_t WG_BUF = WG_A + WG_B;               // 47104
+constexpr uint32_t WG_SMEM = 2 * WG_BUF;               // 94208
+// furthest byte an MMA reads in a buffer: A of the last offset pair's last K step
+static_assert((uint32_t)(((HZ - 1) * HY + (SL_Y - 2) + 2) * WG_ROW) + WG_ROW + 15 * 128 + 128 <= WG_A,
+              "weight-gradient A operand reads past its buffer");
+static_assert((SL_Y - 2) * 256 + 256 + 128 + 128 <= (int)WG_B, "weight-gradient B operand reads past its buffer");
+
 __global__ void __launch_bounds__(128)
-    k_wgrad(const __nv_bfloat16* __restrict__ dy, const __nv_bfloat16* __restrict__ x, const int4* __restrict__ tiles,
-            int n_tiles, Box b, float* __restrict__ part)
+    k_wgrad_tc(const __nv_bfloat16* __restrict__ dy, const __nv_bfloat16* __restrict__ x,
+               const int4* __restrict__ slabs, int n_slabs, Box b, float* __restrict__ part,
+               unsigned int* __restrict__ err)
 {
-    __shared__ __align__(16) __nv_bfloat16 sdy[64 * CH];
-    __shared__ __align__(16) __nv_bfloat16 sx[216 * CH];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[7][2][4];
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ float sdb[128][4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x;
+    const int J = (n_slabs - (int)blockIdx.x + G - 1) / G;  // slabs of this CTA (>= 1)
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_mma[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar_mma[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // nine accumulators of 16 columns at columns 0, 16, ..., 128
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(su32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t tbase = tmem_base;
+    const uint32_t* x32 = reinterpret_cast<const uint32_t*>(x);
+    const uint32_t* dy32 = reinterpret_cast<const uint32_t*>(dy);
+    // lane l holds, of an 8-cell x 8-channel block, cell l / 4 and channels 2 (l % 4), + 1 (one
+    // 32-bit word of the channels-last data); stmatrix .trans writes the block channel by channel
+    // (16 B rows of 8 cells), the canonical core-matrix rows
+    const int ci8 = lane >> 2, cpw = lane & 3;
+    float db[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};  // bias gradient of channels 8 g + 2 cpw + h
+    // slab j's operands into buffer j & 1: warp w transposes halo rows w, w + 4, ... and x rows
+    // w, w + 4, ... of dy.  Every load of the slab is issued before the first store, so the
+    // warp waits for one memory latency per slab, not one per row.
+    constexpr int RW = (WG_HROWS + 3) / 4;  // halo rows per warp (14; warps 2 and 3 have 13)
+    auto stage = [&](int j) {
+        const int4 sl = slabs[blockIdx.x + j * G];
+        const uint32_t A = su32(smem + (j & 1) * WG_BUF), B = A + WG_A;
+        uint32_t v[RW][3][2], u[SL_Y / 4][2];
 #pragma unroll
-    for (int l = 0; l < 7; ++l)
+        for (int i = 0; i < RW; ++i) {
+            const int r = warp + 4 * i;
+            const int Y = sl.y + r % HY, Z = sl.z + r / HY;  // padded coordinates
+            const bool row_ok = r < WG_HROWS && Y < b.py && Z < b.pz;
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[l][j][k] = 0.0f;
-    float dbacc = 0.0f;
-    for (int ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        const int4 tile = tiles[ti];
-        __syncthreads();
-        {
-            const int c = threadIdx.x >> 1, half = threadIdx.x & 1;
-            const int cx = c & 3, cy = (c >> 2) & 3, cz = c >> 4;
-            reinterpret_cast<uint4*>(sdy)[threadIdx.x] = __ldg(
-                reinterpret_cast<const uint4*>(dy + pidx(b, tile.x + cx, tile.y + cy, tile.z + cz) * CH) + half);
+            for (int sx = 0; sx < 3; ++sx) {
+                const int X = sl.x + ci8 + sx;
+                const bool ok = row_ok && X < b.px;
+                const size_t c8 = ok ? (((size_t)Z * b.py + Y) * b.px + X) * (CH / 2) : 0;
+                v[i][sx][0] = ok ? __ldg(x32 + c8 + cpw) : 0u;
+                v[i][sx][1] = ok ? __ldg(x32 + c8 + 4 + cpw) : 0u;
+            }
         }
-        for (int q = threadIdx.x; q < 216 * 2; q += blockDim.x) {
-            const int c = q >> 1, half = q & 1;
-            const int hx = c % 6, hy = (c / 6) % 6, hz = c / 36;
-            reinterpret_cast<uint4*>(sx)[q] = __ldg(
-                reinterpret_cast<const uint4*>(x + pidx(b, tile.x - 1 + hx, tile.y - 1 + hy, tile.z - 1 + hz) * CH) + half);
+#pragma unroll
+        for (int i = 0; i < SL_Y / 4; ++i) {
+            const int X = sl.x + ci8, Y = sl.y + warp + 4 * i;
+            const bool ok = X < b.nx && Y < b.ny;
+            const size_t c8 = ok ? pidx(b, X, Y, sl.z) * (CH / 2) : 0;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) u[i][g] = ok ? __ldg(dy32 + c8 + 4 * g + cpw) : 0u;
         }
+#pragma unroll
+        for (int i = 0; i < RW; ++i) {
+            const int r = warp + 4 * i;
+            if (r >= WG_HROWS) break;  // warp-uniform
+            // blocks (sx, g) at row + 256 sx + 128 g: lane l gives the address of row l % 8 of
+            // block l / 8 (x4: sx = 0, 1) and of block 4 + l / 8 (x2: sx = 2, lanes 0-15)
+            const uint32_t row = A + (uint32_t)r * WG_ROW + 16u * (uint32_t)lane;
+            asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(row),
+                         "r"(v[i][0][0]), "r"(v[i][0][1]), "r"(v[i][1][0]), "r"(v[i][1][1])
+                         : "memory");
+            asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1, %2};" ::"r"(row + 512u * (lane < 16)),
+                         "r"(v[i][2][0]), "r"(v[i][2][1])
+                         : "memory");
+        }
+#pragma unroll
+        for (int i = 0; i < SL_Y / 4; ++i) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                db[g][0] += __uint_as_float(u[i][g] << 16);
+                db[g][1] += __uint_as_float(u[i][g] & 0xFFFF0000u);
+            }
+            const uint32_t row = B + (uint32_t)(warp + 4 * i) * 256u + 16u * (uint32_t)(lane & 15);
+            asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1, %2};" ::"r"(row), "r"(u[i][0]),
+                         "r"(u[i][1])
+                         : "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+    };
+    // the 72 MMAs of slab j (thread 0); a descriptor's start field is the address / 16 (no carry
+    // out of it below 256 KB), so the operands' descriptors are the buffer's plus constants
+    auto issue = [&](int j) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t A = su32(smem + (j & 1) * WG_BUF), B = A + WG_A;
+        const uint64_t a0 = smem_desc(A, WG_ROW, 128), b0 = smem_desc(B, 256, 128);
+        const uint32_t acc = j > 0 ? 1u : 0u;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+#pragma unroll
+            for (int k = 0; k < SL_Y / 2; ++k) {
+                const uint64_t ad = a0 + (uint64_t)(((a / 3) * HY + 2 * k + a % 3) * (int)(WG_ROW >> 4));
+                const uint64_t bd = b0 + (uint64_t)(k * (512 >> 4));
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                    "p;\n}\n" ::"r"(tbase + 16u * (uint32_t)a),
+                    "l"(ad), "l"(bd), "r"(CONV_IDESC), "r"(k > 0 ? 1u : acc)
+                    : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&bar_mma[j & 1]))
+                     : "memory");
+    };
+    bool ok = true;
+    int issued = 0;  // MMA groups issued (the same count in every thread)
+    for (int j = 0; j < J; ++j) {
+        if (j >= 2) {  // buffer j & 1 is free once the MMAs of slab j - 2 are done
+            const int p = j - 2;
+            if (!__syncthreads_and(tc_wait(&bar_mma[p & 1], (p >> 1) & 1))) {
+                ok = false;
+                break;
+            }
+        }
+        stage(j);
         __syncthreads();
-        if (threadIdx.x < CH)
-            for (int c = 0; c < 64; ++c) dbacc += __bfloat162float(sdy[c * CH + threadIdx.x]);
+        if (tid == 0) issue(j);
+        ++issued;
+    }
+    // the last group's completion covers every MMA issued before it
+    if (ok && !__syncthreads_and(tc_wait(&bar_mma[(J - 1) & 1], ((J - 1) >> 1) & 1))) ok = false;
+    if (!ok) {
+        if (tid == 0) atomicOr(err, 1u);
+        // bounded waits for the groups that may still be in flight, so that the tensor memory is
+        // idle when it is freed
+        for (int p = issued >= 2 ? issued - 2 : 0; p < issued; ++p) tc_wait(&bar_mma[p & 1], (p >> 1) & 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float* dW = part + (size_t)blockIdx.x * (NW + CH);
+        if (warp < 2) {
+            const int m = warp * 32 + lane, sx = m >> 4, ci = m & 15;
+#pragma unroll 1
+            for (int a = 0; a < 9; ++a) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(tbase + 16u * (uint32_t)a + ((uint32_t)(warp * 32) << 16)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (sx < 3) {
+                    const int o = sx + 3 * (a % 3) + 9 * (a / 3);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            // A[m = co][k = cell c of slab z = s] = dy[cell][co]
-            const int k0 = s * 16 + 2 * t, k1 = k0 + 8;
-            uint32_t a[4];
-            a[0] = pack2(sdy[k0 * CH + g], sdy[(k0 + 1) * CH + g]);
-            a[1] = pack2(sdy[k0 * CH + g + 8], sdy[(k0 + 1) * CH + g + 8]);
-            a[2] = pack2(sdy[k1 * CH + g], sdy[(k1 + 1) * CH + g]);
-            a[3] = pack2(sdy[k1 * CH + g + 8], sdy[(k1 + 1) * CH + g + 8]);
-#pragma unroll
-            for (int l = 0; l < 7; ++l) {
-                const int o = warp + 4 * l;
-                if (o >= 27) continue;
-                const int dx = o % 3 - 1, dyy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-                // B[k = cell c][n = ci] = x[cell(c) + o][ci], halo cell of cell c
-                auto hidx = [&](int c) {
-                    return ((s + 1 + dz) * 6 + ((c >> 2) + 1 + dyy)) * 6 + ((c & 3) + 1 + dx);
-                };
-                const int h0 = hidx(2 * t), h1 = hidx(2 * t + 1), h2 = hidx(2 * t + 8), h3 = hidx(2 * t + 9);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int n = 8 * j + g;
-                    uint32_t bb[2];
-                    bb[0] = pack2(sx[h0 * CH + n], sx[h1 * CH + n]);
-                    bb[1] = pack2(sx[h2 * CH + n], sx[h3 * CH + n]);
-                    mma16816(acc[l][j], a, bb);
+                    for (int co = 0; co < CH; ++co) dW[(o * CH + co) * CH + ci] = __uint_as_float(r[co]);
                 }
             }
         }
-    }
-    float* dW = part + (size_t)blockIdx.x * (NW + CH);
-#pragma unroll
-    for (int l = 0; l < 7; ++l) {
-        const int o = warp + 4 * l;
-        if (o >= 27) continue;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int ci = 8 * j + 2 * t;
-            dW[(o * CH + g) * CH + ci] = acc[l][j][0];
-            dW[(o * CH + g) * CH + ci + 1] = acc[l][j][1];
-            dW[(o * CH + g + 8) * CH + ci] = acc[l][j][2];
-            dW[(o * CH + g + 8) * CH + ci + 1] = acc[l][j][3];
+        sdb[tid][0] = db[0][0];
+        sdb[tid][1] = db[0][1];
+        sdb[tid][2] = db[1][0];
+        sdb[tid][3] = db[1][1];
+        __syncthreads();
+        if (tid < CH) {  // channel 8 g + 2 c + h: the threads with tid' % 4 = c, in increasing tid'
+            const int g = tid >> 3, c = (tid >> 1) & 3, h = tid & 1;
+            float acc = 0.0f;
+            for (int t = c; t < 128; t += 4) acc += sdb[t][2 * g + h];
+            dW[NW + tid] = acc;
         }
     }
-    if (threadIdx.x < CH) dW[NW + threadIdx.x] = dbacc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase) : "memory");
 }
 
-// out[k] = sum over the n_part partial gradients of part[p][k] in increasing p (weights and
-// biases of one layer, NW + CH values).
-__global__ void __launch_bounds__(256)
+// out[k] = sum over the n_part partial gradients of part[p][k] (weights and biases of one layer,
+// NW + CH values), in a fixed order: a CTA takes 32 consecutive k; its thread (c, k) adds the
+// partials p = c, c + 8, ... in increasing p, and the eight chunk sums are then added in
+// increasing c.
+constexpr int WR_K = 32, WR_C = 8;
+__global__ void __launch_bounds__(WR_K * WR_C)
     k_wgrad_reduce(const float* __restrict__ part, int n_part, float* __restrict__ out)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= NW + CH) return;
+    __shared__ float cs[WR_C][WR_K];
+    const int kk = threadIdx.x % WR_K, c = threadIdx.x / WR_K;
+    const int k = blockIdx.x * WR_K + kk;
     float s = 0.0f;
-    for (int p = 0; p < n_part; ++p) s += part[(size_t)p * (NW + CH) + k];
-    out[k] = s;
+    if (k < NW + CH) {
+#pragma unroll 8
+        for (int p = c; p < n_part; p += WR_C) s += part[(size_t)p * (NW + CH) + k];
+    }
+    cs[c][kk] = s;
+    __syncthreads();
+    if (c == 0 && k < NW + CH) {
+        float t = cs[0][kk];
+#pragma unroll
+        for (int q = 1; q < WR_C; ++q) t += cs[q][kk];
+        out[k] = t;
+    }
 }
 
 // The elementwise kernels of the corrector run over the slabs of the convolutions (one CTA of
@@ -585,8 +701,7 @@ struct lbm_corrector {
     void* ctx = nullptr;
     std::vector<void*> owned;
     uint8_t* mask = nullptr;
-    int4* tiles = nullptr;   // 4^3 tiles with fluid, dilated by one tile (weight gradients)
-    int4* slabs = nullptr;   // 8 x 16 x 1 slabs covering those tiles (convolutions)
+    int4* slabs = nullptr;   // 8 x 16 x 1 slabs covering the 4^3 tiles with fluid, dilated by one tile
     int64_t n_slabs = 0;
     unsigned int* err = nullptr;  // set by a conv CTA whose bounded wait gave up
     cudaEvent_t ev = nullptr;     // orders the corrector's stream and a domain's stream (apply)
@@ -675,12 +790,13 @@ struct lbm_corrector {
             k_loss<<<(unsigned)n_slabs, 128, 0, stream>>>(o4, uu, ut, mk, box, 1.0f / du_scale, count, dO, loss, slabs);
         }
         e = cudaGetLastError();
-        const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_tiles, 1), WG_CTAS);
+        const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_slabs, 1), WG_CTAS);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM);
         // weight gradient of one layer: per-CTA partials, then their sum in a fixed order
         auto wgrad = [&](const __nv_bfloat16* g, const __nv_bfloat16* xin, float* out) {
-            if (!n_tiles) return cudaSuccess;
-            k_wgrad<<<wg, 128, 0, stream>>>(g, xin, tiles, (int)n_tiles, box, wpart);
-            k_wgrad_reduce<<<blocks(NW + CH, 256), 256, 0, stream>>>(wpart, wg, out);
+            if (!n_slabs) return cudaSuccess;
+            k_wgrad_tc<<<wg, 128, WG_SMEM, stream>>>(g, xin, slabs, (int)n_slabs, box, wpart, err);
+            k_wgrad_reduce<<<blocks(NW + CH, WR_K), WR_K * WR_C, 0, stream>>>(wpart, wg, out);
             return cudaGetLastError();
         };
         if (e == cudaSuccess) e = wgrad(dO, y2, grad + 2 * (NW + CH));
@@ -773,7 +889,6 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
         return p;
     };
     K->mask = static_cast<uint8_t*>(D(cells));
-    K->tiles = static_cast<int4*>(D(sizeof(int4) * std::max<size_t>(tl.size(), 1)));
     K->slabs = static_cast<int4*>(D(sizeof(int4) * std::max<size_t>(sv.size(), 1)));
     K->err = static_cast<unsigned int*>(D(sizeof(unsigned int)));
     K->x0 = static_cast<__nv_bfloat16*>(D(act));
@@ -801,8 +916,6 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
         return nn_fail(LBM_ERR_OOM, "allocation failed: corrector buffers");
     }
     cudaError_t e = cudaMemcpyAsync(K->mask, mask, cells, cudaMemcpyHostToDevice, K->stream);
-    if (e == cudaSuccess && !tl.empty())
-        e = cudaMemcpyAsync(K->tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, K->stream);
     if (e == cudaSuccess && !sv.empty())
         e = cudaMemcpyAsync(K->slabs, sv.data(), sizeof(int4) * sv.size(), cudaMemcpyHostToDevice, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->err, 0, sizeof(unsigned int), K->stream);

@@ -46,10 +46,10 @@ def _case(n=16, seed=0):
 
 def _multi_slab_case(seed=0):
     """A 48 x 64 x 64 box (x, y, z) holding an ellipsoidal vessel with a cylindrical obstacle:
-    1504 slabs of 8 x 16 x 1 cells and 2688 active 4^3 tiles, so that every persistent CTA of
-    the convolution (4 per SM) runs at least two slabs -- the double-buffered halo, both tensor
-    memory accumulators and the mbarrier phase flips -- and every weight-gradient CTA loops over
-    several tiles."""
+    1504 slabs of 8 x 16 x 1 cells (2688 active 4^3 tiles), so that every persistent CTA of the
+    convolution (4 per SM) runs at least two slabs -- the double-buffered halo, both tensor
+    memory accumulators and the mbarrier phase flips -- and so does every weight-gradient CTA
+    (at most 304: both staging buffers, accumulators carried over slabs)."""
     rng = np.random.default_rng(seed)
     nz, ny, nx = 64, 64, 48
     z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
@@ -84,7 +84,7 @@ def test_multi_slab_case_covers_every_cta_twice():
     slabs, tiles = conv_work_counts(mask)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert slabs >= 2 * 4 * sms, (slabs, sms)
-    assert tiles >= 4 * 304
+    assert slabs >= 2 * 304  # every weight-gradient CTA (at most 304) walks two or more slabs
 
 
 def _t(a):
@@ -138,8 +138,9 @@ def test_forward_matches_oracle_multi_slab():
 
 
 def test_gradients_match_oracle_multi_slab():
-    """Loss and weight gradients where every convolution CTA (forward and data gradient) walks
-    two or more slabs and every weight-gradient CTA loops over several tiles."""
+    """Loss and weight gradients where every convolution CTA (forward and data gradient) and
+    every weight-gradient CTA walks two or more slabs (double-buffered staging, tensor-memory
+    accumulators carried over slabs)."""
     mask, rho, u, ut, params = _multi_slab_case(1)
     net = lbm.Corrector(mask, params, US, RS, DS)
     loss, grads = net.gradients(_t(rho), _t(u), _t(ut))
