@@ -185,13 +185,14 @@ struct Store<LBM_STORE_BF16> {
 template <int ST>
 __device__ __forceinline__ void scale_in(float (&d)[Q])
 {
-    if (!Store<ST>::SCALED) return;
+    if constexpr (Store<ST>::SCALED) {
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const float2 v = __fmul2_rn(make_float2(d[j], d[j + 18]), make_float2(w_of(j), w_of(j)));
-        d[j] = v.x;
-        d[j + 18] = v.y;
-        d[j + 9] = d[j + 9] * w_of(j + 9);
+        for (int j = 0; j < 9; ++j) {
+            const float2 v = __fmul2_rn(make_float2(d[j], d[j + 18]), make_float2(w_of(j), w_of(j)));
+            d[j] = v.x;
+            d[j + 18] = v.y;
+            d[j + 9] = d[j + 9] * w_of(j + 9);
+        }
     }
 }
 
@@ -1392,7 +1393,8 @@ __global__ void __launch_bounds__(256)
     const int64_t b = fl_box[k];
     const uint32_t slot = (uint32_t)fl_slot[k];
     // open-boundary cells are left alone: their closures rebuild the unknowns every step
-    if (((v.word[slot] >> WORD_KIND_SHIFT) & 3u) >= KIND_INLET) return;
+    const uint32_t word = v.word[slot];
+    if (((word >> WORD_KIND_SHIFT) & 3u) >= KIND_INLET) return;
     const float rho = rho_in[b];
     float ps[3][3], dp[3][3];
 #pragma unroll
@@ -1414,34 +1416,39 @@ __global__ void __launch_bounds__(256)
         const float by = ps[1][iy] + dp[1][iy], bz = ps[2][iz] + dp[2][iz];
         delta[i] = rho * (dp[0][ix] * by * bz + ps[0][ix] * dp[1][iy] * bz + ps[0][ix] * ps[1][iy] * dp[2][iz]);
     }
+    // every read is issued before the first write: the compiler cannot tell that a write does not
+    // alias the next read, so read-modify-write pairs in one loop would wait for one memory
+    // latency each
     const uint32_t n = (uint32_t)v.n_slots;
+    uint32_t off[Q];
+    float f[Q];
     if (SCHEME == LBM_SCHEME_ESOTERIC) {
         uint32_t cs[8];
         corner_slots(v.nb8 + (slot / BRICK_CELLS) * 8, slot, cs);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const uint32_t dir = parity_prev ? (uint32_t)i : (uint32_t)(Q - 1 - i);
-            const uint32_t off = dir * n + cs[corner_pos(i)];
-            if (LBM_IN_RANGE(off, (uint64_t)Q * n, 7)) Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
-        }
-        const uint32_t word = v.word[slot];
-        if (((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI) {
-            const uint32_t off0 = (uint32_t)v.aux[slot];
-            const uint32_t wm = word & WORD_WALL_MASK;
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                if (((wm >> i) & 1u) && LBM_IN_RANGE(link_index(off0, wm, i), v.n_bq, 5)) {
-                    const uint32_t off = link_index(off0, wm, i);
-                    Store<ST>::store(v.side, i, off, Store<ST>::load_rw(v.side, i, off) + delta[i]);
-                }
-        }
+        for (int i = 0; i < Q; ++i) off[i] = (parity_prev ? (uint32_t)i : (uint32_t)(Q - 1 - i)) * n + cs[corner_pos(i)];
     } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const uint32_t off = (uint32_t)i * n + slot;
-            if (LBM_IN_RANGE(off, (uint64_t)Q * n, 7)) Store<ST>::store(pop, i, off, Store<ST>::load_rw(pop, i, off) + delta[i]);
-        }
+        for (int i = 0; i < Q; ++i) off[i] = (uint32_t)i * n + slot;
     }
+    const bool bouzidi = SCHEME == LBM_SCHEME_ESOTERIC && ((word >> WORD_KIND_SHIFT) & 3u) == KIND_BOUZIDI;
+    const uint32_t wm = bouzidi ? (word & WORD_WALL_MASK) : 0u;
+    const uint32_t off0 = bouzidi ? (uint32_t)v.aux[slot] : 0u;
+    float fs[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = LBM_IN_RANGE(off[i], (uint64_t)Q * n, 7) ? Store<ST>::load_rw(pop, i, off[i]) : 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        fs[i] = (((wm >> i) & 1u) && LBM_IN_RANGE(link_index(off0, wm, i), v.n_bq, 5))
+                    ? Store<ST>::load_rw(v.side, i, link_index(off0, wm, i))
+                    : 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (LBM_IN_RANGE(off[i], (uint64_t)Q * n, 7)) Store<ST>::store(pop, i, off[i], f[i] + delta[i]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (((wm >> i) & 1u) && LBM_IN_RANGE(link_index(off0, wm, i), v.n_bq, 5))
+            Store<ST>::store(v.side, i, link_index(off0, wm, i), fs[i] + delta[i]);
 }
 
 // FP64 diagnostics: per-block partial sums in a fixed order; one block then reduces the
@@ -1600,6 +1607,10 @@ cudaError_t launch_step(int scheme, int config, const DomainView& v, const void*
                                          : launch_step_scheme<ST, LBM_SCHEME_AB>(config, v, src, dst, a, s);
 }
 
+// the export and the correction run one thread per fluid cell; with small CTAs a domain of a few
+// ten thousand cells still spreads over every SM (its latency chains overlap on all of them)
+constexpr int PER_CELL_THREADS = 64;
+
 template <int ST>
 cudaError_t launch_macroscopic(int scheme, const DomainView& v, const void* src, const LevelArgs& a,
                                const int32_t* fl_slot, const int32_t* fl_box, int64_t n_fluid, int dense, float* rho,
@@ -1607,10 +1618,10 @@ cudaError_t launch_macroscopic(int scheme, const DomainView& v, const void* src,
 {
     if (n_fluid == 0) return cudaSuccess;
     if (scheme == LBM_SCHEME_ESOTERIC)
-        k_macroscopic<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, src, a, fl_slot, fl_box,
+        k_macroscopic<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, PER_CELL_THREADS), PER_CELL_THREADS, 0, s>>>(v, src, a, fl_slot, fl_box,
                                                                                   n_fluid, dense, rho, u, n_out);
     else
-        k_macroscopic<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, src, a, fl_slot, fl_box, n_fluid,
+        k_macroscopic<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, PER_CELL_THREADS), PER_CELL_THREADS, 0, s>>>(v, src, a, fl_slot, fl_box, n_fluid,
                                                                             dense, rho, u, n_out);
     return cudaGetLastError();
 }
@@ -1673,10 +1684,10 @@ cudaError_t launch_apply_du(int scheme, const DomainView& v, void* pop, int pari
 {
     if (n_fluid == 0) return cudaSuccess;
     if (scheme == LBM_SCHEME_ESOTERIC)
-        k_apply_du<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, pop, parity_prev, fl_slot, fl_box,
+        k_apply_du<ST, LBM_SCHEME_ESOTERIC><<<grid_for(n_fluid, PER_CELL_THREADS), PER_CELL_THREADS, 0, s>>>(v, pop, parity_prev, fl_slot, fl_box,
                                                                                n_fluid, rho, u, du, n_box);
     else
-        k_apply_du<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, 256), 256, 0, s>>>(v, pop, parity_prev, fl_slot, fl_box, n_fluid,
+        k_apply_du<ST, LBM_SCHEME_AB><<<grid_for(n_fluid, PER_CELL_THREADS), PER_CELL_THREADS, 0, s>>>(v, pop, parity_prev, fl_slot, fl_box, n_fluid,
                                                                          rho, u, du, n_box);
     return cudaGetLastError();
 }

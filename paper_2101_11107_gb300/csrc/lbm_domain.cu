@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,7 @@ lbm_status debug_status(int storage)
 
 struct lbm_domain {
     int32_t nx = 0, ny = 0, nz = 0;
+    uint64_t serial = 0;  // unique per domain of the process (never reused, unlike an address)
     lbm_params params{};
     int64_t n_fluid = 0, n_bricks = 0, n_store_bricks = 0, n_slots = 0, n_bq = 0, n_io = 0, n_wall = 0;
     int64_t n_blinks = 0;  // wall links of the Bouzidi cells (length of the packed link lists)
@@ -514,6 +516,8 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, int32_
 
     // ---------------------------------------------------------------- device
     lbm_domain* D = new (std::nothrow) lbm_domain();
+    static std::atomic<uint64_t> next_serial{1};
+    if (D) D->serial = next_serial.fetch_add(1);
     if (!D) return fail(LBM_ERR_OOM, "host allocation failed");
     D->nx = nx;
     D->ny = ny;
@@ -917,6 +921,18 @@ lbm_status lbm_probe(lbm_domain* D, const int64_t* fluid_index, int32_t n, float
 }  // extern "C"
 
 namespace lbm {
+cudaError_t enqueue_macroscopic_dense(lbm_domain* D, float* rho, float* u, bool clear)
+{
+    const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
+    cudaError_t e = cudaSuccess;
+    if (clear) e = cudaMemsetAsync(rho, 0, sizeof(float) * n_box, D->stream);
+    if (clear && e == cudaSuccess) e = cudaMemsetAsync(u, 0, sizeof(float) * 3 * n_box, D->stream);
+    if (e != cudaSuccess) return e;
+    return launchers(D->params.storage)
+        .macroscopic(D->params.scheme, D->view, D->src(), D->level_args(D->time), D->d_fl_slot, D->d_fl_box,
+                     D->n_fluid, 1, rho, u, n_box, D->stream);
+}
+
 cudaError_t enqueue_velocity_correction(lbm_domain* D, const float* rho, const float* u, const float* du)
 {
     const int64_t n_box = (int64_t)D->nx * D->ny * D->nz;
@@ -1545,6 +1561,7 @@ bool domain_access(const lbm_domain* D, DomainAccess* out)
     out->n_fluid = D->n_fluid;
     out->time = D->time;
     out->stream = D->stream;
+    out->serial = D->serial;
     return true;
 }
 

@@ -196,8 +196,13 @@ struct DomainAccess {
     int64_t n_fluid;
     int64_t time;
     cudaStream_t stream;
+    uint64_t serial;  // unique per domain of the process
 };
 bool domain_access(const lbm_domain* dom, DomainAccess* out);
+// the dense export of lbm_get_macroscopic on the domain's stream; clear = false leaves the
+// cells that are not fluid as they are (a caller whose arrays already hold this domain's zeros
+// there)
+cudaError_t enqueue_macroscopic_dense(lbm_domain* dom, float* rho, float* u, bool clear);
 // the velocity correction of lbm_apply_velocity_correction with the current level's rho and u
 // already exported (dense device arrays, as lbm_get_macroscopic writes them): enqueued on the
 // domain's stream

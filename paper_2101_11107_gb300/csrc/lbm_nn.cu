@@ -48,6 +48,16 @@ __device__ __forceinline__ size_t pidx(const Box& b, int x, int y, int z)
     return ((size_t)(z + 1) * b.py + (size_t)(y + 1)) * b.px + (size_t)(x + 1);
 }
 
+// du = du_scale * clamp(O[0:3], -clip, clip) at the masked cells of the slabs, 0 at their other
+// cells (three planes; the caller zeroes the rest of the box).  The clamp lets a NaN through
+// (fminf/fmaxf would turn it into -clip): a network that has gone non-finite must make the
+// corrected state non-finite, which the caller's fallback detects, not apply a full-size
+// correction everywhere.
+__device__ __forceinline__ float clamp_keep_nan(float o, float clip)
+{
+    return o > clip ? clip : (o < -clip ? -clip : o);
+}
+
 // ------------------------------------------------------------------------------ tcgen05 conv
 // out[p][co] = act(sum_o sum_ci w[o][co][ci] in[p + o][ci] + bias[co]), zeroed where gate <= 0,
 // as an implicit GEMM on the 5th-generation tensor cores.  A slab is 8 (x) x 16 (y) x 1 (z)
@@ -64,8 +74,9 @@ __device__ __forceinline__ size_t pidx(const Box& b, int x, int y, int z)
 //     8-row core matrices are 8 consecutive cells along x (16 B apart), core matrices along M
 //     are the 16 y rows (160 B apart), and the two K core matrices are the two planes.  No
 //     gather, no copy: the 27 descriptors differ only in their start address.
-//   * B (the 27 weight blocks, N x K = 16 x 16) is staged in the same canonical layout (core
-//     matrix (n-group, k-group) at 128-byte steps).
+//   * B (the 27 weight blocks, N x K = 16 x 16) is stored in global memory in the same canonical
+//     layout (core matrix (n-group, k-group) at 128-byte steps; k_prepare writes it) and comes in
+//     with the first halo by one bulk copy.
 //   * The epilogue reads each row back with tcgen05.ld (warp w owns lanes 32w..32w+31), adds the
 //     bias, applies ReLU and the gate, and writes 32 bytes per cell.
 // Every wait (TMA, MMA completion) is bounded; on a timeout the CTA flags the error, waits for
@@ -76,7 +87,8 @@ constexpr uint32_t PLANE_BYTES = HX * HY * HZ * 16;     // 8640: one TMA box
 constexpr uint32_t PLANE_STRIDE = 8704;                 // 128-byte aligned plane step
 constexpr uint32_t HALO_BYTES = 2 * PLANE_STRIDE;       // one halo buffer: two planes
 constexpr uint32_t W_OFF = 2 * HALO_BYTES;              // weights after the two halo buffers
-constexpr uint32_t CONV_SMEM = W_OFF + 27 * 512;        // 48640 B
+constexpr uint32_t W_BYTES = 27 * 512;                  // one layer's weights, BF16
+constexpr uint32_t CONV_SMEM = W_OFF + W_BYTES;         // 48640 B
 constexpr int CONV_CTAS_PER_SM = 4;
 constexpr int TC_WAIT_LIMIT = 1 << 22;
 
@@ -106,11 +118,20 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
     return false;
 }
 
-template <bool OUT_F32>
+// Output of a convolution: BF16 activations (padded, channels-last), FP32 O[0:4] (compact float4
+// per cell), or the velocity correction du = scale clamp(O[0:3]) at the cells of `mask` (0 at the
+// slabs' other cells; three planes) -- the last layer of an inference with the output step fused.
+enum ConvOut { OUT_BF16 = 0, OUT_F32 = 1, OUT_DU = 2 };
+struct DuArgs {
+    const uint8_t* mask;
+    float scale, clip;
+};
+
+template <int OUT>
 __global__ void __launch_bounds__(128)
     k_conv_tc(const __grid_constant__ CUtensorMap tin, const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
               int relu, const __nv_bfloat16* __restrict__ gate, void* __restrict__ out, const int4* __restrict__ slabs,
-              int n_slabs, Box b, unsigned int* __restrict__ err)
+              int n_slabs, Box b, unsigned int* __restrict__ err, DuArgs dua)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_tma[2], bar_mma[2];
@@ -134,12 +155,20 @@ __global__ void __launch_bounds__(128)
     __syncthreads();
     // halo of slab j into buffer j & 1: padded coordinates (x0, y0, z) .. + (9, 17, 2), channels
     // 0-7 and 8-15 (issued by thread 0)
+    // (slab 0 also brings the weights: one bulk copy, already in the shared-memory layout)
     auto load_halo = [&](int j) {
         const int4 sl = slabs[blockIdx.x + j * G];
         uint64_t* bar = &bar_tma[j & 1];
         unsigned char* dst = smem + (j & 1) * HALO_BYTES;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(2u * PLANE_BYTES)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+                     "r"(2u * PLANE_BYTES + (j == 0 ? W_BYTES : 0u))
                      : "memory");
+        if (j == 0)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    su32(smem + W_OFF)),
+                "l"(w), "r"(W_BYTES), "r"(su32(bar))
+                : "memory");
 #pragma unroll
         for (int c = 0; c < 2; ++c)
             asm volatile(
@@ -152,14 +181,6 @@ __global__ void __launch_bounds__(128)
         load_halo(0);
         if (J > 1) load_halo(1);
     }
-    // weights: chunk (o, co, j) = w[o][co][8j..8j+7] -> core matrix (co / 8, j) of block o
-    for (int q = tid; q < 27 * 16 * 2; q += 128) {
-        const int o = q >> 5, co = (q >> 1) & 15, j = q & 1;
-        *reinterpret_cast<uint4*>(smem + W_OFF + o * 512 + (2 * (co >> 3) + j) * 128 + (co & 7) * 16) =
-            __ldg(reinterpret_cast<const uint4*>(w) + q);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights visible to the tensor cores
-    __syncthreads();
     const uint32_t tbase = tmem_base;
     float bz[CH];
 #pragma unroll
@@ -180,16 +201,29 @@ __global__ void __launch_bounds__(128)
         if (x < b.nx && y < b.ny) {
             float v[CH];
             const size_t pc = pidx(b, x, y, z);
+            uint4 gw[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+            if (gate) {  // the gate's 16 channels of this cell, two 16-byte loads
+                gw[0] = __ldg(reinterpret_cast<const uint4*>(gate + pc * CH));
+                gw[1] = __ldg(reinterpret_cast<const uint4*>(gate + pc * CH) + 1);
+            }
+            const uint32_t* g32 = reinterpret_cast<const uint32_t*>(gw);
 #pragma unroll
             for (int co = 0; co < CH; ++co) {
                 float t = __uint_as_float(r[co]) + bz[co];
                 if (relu) t = fmaxf(t, 0.0f);
-                if (gate && !(__bfloat162float(gate[pc * CH + co]) > 0.0f)) t = 0.0f;
+                const uint32_t gb = (co & 1) ? (g32[co >> 1] & 0xFFFF0000u) : (g32[co >> 1] << 16);
+                if (gate && !(__uint_as_float(gb) > 0.0f)) t = 0.0f;
                 v[co] = t;
             }
-            if (OUT_F32) {
-                *reinterpret_cast<float4*>(static_cast<float*>(out) + (((size_t)z * b.ny + y) * b.nx + x) * 4) =
-                    make_float4(v[0], v[1], v[2], v[3]);
+            const size_t c = ((size_t)z * b.ny + y) * b.nx + x;
+            if (OUT == OUT_F32) {
+                *reinterpret_cast<float4*>(static_cast<float*>(out) + c * 4) = make_float4(v[0], v[1], v[2], v[3]);
+            } else if (OUT == OUT_DU) {
+                const size_t n = (size_t)b.nx * b.ny * b.nz;
+                const bool on = dua.mask[c] != 0;
+                float* du = static_cast<float*>(out);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) du[k * n + c] = on ? clamp_keep_nan(v[k], dua.clip) * dua.scale : 0.0f;
             } else {
                 uint32_t pk[8];
 #pragma unroll
@@ -221,13 +255,16 @@ __global__ void __launch_bounds__(128)
         }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = su32(smem + (j & 1) * HALO_BYTES), w0 = su32(smem + W_OFF);
+            // a descriptor's start field is the address / 16 (no carry out of it below 256 KB): the
+            // 27 offsets' descriptors are the buffer's plus constants
+            const uint64_t a0 = smem_desc(su32(smem + (j & 1) * HALO_BYTES), PLANE_STRIDE, HX * 16);
+            const uint64_t w0 = smem_desc(su32(smem + W_OFF), 128, 256);
             const uint32_t d = tbase + 32u * (uint32_t)(j & 1);
-#pragma unroll 1
+#pragma unroll
             for (int o = 0; o < 27; ++o) {
-                const uint32_t ox = o % 3, oy = (o / 3) % 3, oz = o / 9;
-                const uint64_t ad = smem_desc(a0 + 16u * ((oz * HY + oy) * HX + ox), PLANE_STRIDE, HX * 16);
-                const uint64_t bd = smem_desc(w0 + 512u * (uint32_t)o, 128, 256);
+                const int ox = o % 3, oy = (o / 3) % 3, oz = o / 9;
+                const uint64_t ad = a0 + (uint64_t)((oz * HY + oy) * HX + ox);
+                const uint64_t bd = w0 + (uint64_t)(32 * o);
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
                     "p;\n}\n" ::"r"(d),
@@ -529,30 +566,6 @@ __global__ void __launch_bounds__(128) k_features(const float* __restrict__ rho,
     dst[1] = *reinterpret_cast<uint4*>(&v[8]);
 }
 
-// du = du_scale * clamp(O[0:3], -clip, clip) at the masked cells of the slabs, 0 at their other
-// cells (three planes; the caller zeroes the rest of the box).  The clamp lets a NaN through
-// (fminf/fmaxf would turn it into -clip): a network that has gone non-finite must make the
-// corrected state non-finite, which the caller's fallback detects, not apply a full-size
-// correction everywhere.
-__device__ __forceinline__ float clamp_keep_nan(float o, float clip)
-{
-    return o > clip ? clip : (o < -clip ? -clip : o);
-}
-
-__global__ void __launch_bounds__(128) k_output(const float* __restrict__ o4, const uint8_t* __restrict__ mask, Box b,
-                                                float du_scale, float clip, float* __restrict__ du,
-                                                const int4* __restrict__ slabs)
-{
-    int x, y, z;
-    int64_t c;
-    if (!slab_cell(slabs, b, x, y, z, c)) return;
-    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
-    const bool on = mask[c] != 0;
-    du[c] = on ? clamp_keep_nan(o4[c * 4 + 0], clip) * du_scale : 0.0f;
-    du[n + c] = on ? clamp_keep_nan(o4[c * 4 + 1], clip) * du_scale : 0.0f;
-    du[2 * n + c] = on ? clamp_keep_nan(o4[c * 4 + 2], clip) * du_scale : 0.0f;
-}
-
 // Loss = mean over fluid cells and components of (O - T)^2, T = (u_target - u) / du_scale;
 // dO = 2 (O - T) / N at fluid cells (BF16, padded, channels 0..2).
 __global__ void __launch_bounds__(128) k_count(const uint8_t* __restrict__ mask, Box b, const int4* __restrict__ slabs,
@@ -598,8 +611,16 @@ __global__ void __launch_bounds__(128) k_loss(const float* __restrict__ o4, cons
     if (threadIdx.x == 0) atomicAdd(loss, (sh[0] + sh[1]) + (sh[2] + sh[3]));
 }
 
+// Position of weight (o, co, ci) in a layer's BF16 block, which is the convolution's shared-memory
+// layout (copied in as is): block o of 512 B holds the core matrices (co / 8, ci / 8) at 128-byte
+// steps, row co % 8 at 16-byte steps, ci % 8 within the row.
+__device__ __forceinline__ int w_layout(int o, int co, int ci)
+{
+    return o * 256 + (2 * (co >> 3) + (ci >> 3)) * 64 + (co & 7) * 8 + (ci & 7);
+}
+
 // BF16 forward weights and, for layers 2 and 3, the data-gradient kernels
-// wt[o'][ci][co] = w[26 - o'][co][ci] (flipped offsets, transposed channels).
+// wt[o'][ci][co] = w[26 - o'][co][ci] (flipped offsets, transposed channels), both in w_layout.
 __global__ void k_prepare(const float* __restrict__ master, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -607,8 +628,8 @@ __global__ void k_prepare(const float* __restrict__ master, __nv_bfloat16* __res
     const int l = i / NW, r = i % NW;
     const int o = r / (CH * CH), co = (r / CH) % CH, ci = r % CH;
     const float v = master[l * (NW + CH) + r];
-    wb[i] = __float2bfloat16_rn(v);
-    wt[l * NW + ((26 - o) * CH + ci) * CH + co] = __float2bfloat16_rn(v);
+    wb[l * NW + w_layout(o, co, ci)] = __float2bfloat16_rn(v);
+    wt[l * NW + w_layout(26 - o, ci, co)] = __float2bfloat16_rn(v);
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -716,6 +737,8 @@ struct lbm_corrector {
     double* loss = nullptr;
     unsigned long long* count = nullptr;
     int64_t adam_t = 0;
+    int sms = 0;  // SMs of the device the corrector was created on
+    uint64_t export_serial = 0;  // the domain whose zeros rho, u hold outside its fluid cells (0: none)
 
     void* dev(size_t bytes)
     {
@@ -743,20 +766,15 @@ struct lbm_corrector {
     float* bmaster(int l) { return master + (size_t)l * (NW + CH) + NW; }
 
     cudaError_t conv(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, int relu,
-                     const __nv_bfloat16* gate, void* out, bool f32)
+                     const __nv_bfloat16* gate, void* out, int mode, DuArgs dua = DuArgs{nullptr, 0.0f, 0.0f})
     {
         if (n_slabs == 0) return cudaSuccess;
         int t = 0;
         while (t < 5 && tmap_of[t] != in) ++t;
         if (t == 5) return cudaErrorInvalidValue;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int grid = (int)std::min<int64_t>(n_slabs, (int64_t)sms * CONV_CTAS_PER_SM);
-        auto k = f32 ? k_conv_tc<true> : k_conv_tc<false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CONV_SMEM);
-        if (e != cudaSuccess) return e;
-        k<<<grid, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, (int)n_slabs, box, err);
+        auto k = mode == OUT_F32 ? k_conv_tc<OUT_F32> : mode == OUT_DU ? k_conv_tc<OUT_DU> : k_conv_tc<OUT_BF16>;
+        k<<<grid, 128, CONV_SMEM, stream>>>(tmaps[t], w, bias, relu, gate, out, slabs, (int)n_slabs, box, err, dua);
         return cudaGetLastError();
     }
     // nonzero device error word (read after the stream has been synchronised)
@@ -767,15 +785,19 @@ struct lbm_corrector {
         if (h) cudaMemset(err, 0, sizeof(h));
         return h != 0;
     }
-    cudaError_t forward(const uint8_t* cmask, const float* r, const float* uu)
+    // the network on the slabs: O into o4 (du == nullptr), or, for an inference, the correction
+    // du = scale clamp(O[0:3]) at the cells of out_mask straight from the last layer
+    cudaError_t forward(const uint8_t* cmask, const float* r, const float* uu, float* du = nullptr,
+                        const uint8_t* out_mask = nullptr, float scale = 0.0f)
     {
         if (n_slabs == 0) return cudaSuccess;
         k_features<<<(unsigned)n_slabs, 128, 0, stream>>>(r, uu, cmask ? cmask : mask, box, 1.0f / u_scale,
                                                           1.0f / rho_scale, x0, slabs);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = conv(x0, wb, bmaster(0), 1, nullptr, y1, false);
-        if (e == cudaSuccess) e = conv(y1, wb + NW, bmaster(1), 1, nullptr, y2, false);
-        if (e == cudaSuccess) e = conv(y2, wb + 2 * NW, bmaster(2), 0, nullptr, o4, true);
+        if (e == cudaSuccess) e = conv(x0, wb, bmaster(0), 1, nullptr, y1, OUT_BF16);
+        if (e == cudaSuccess) e = conv(y1, wb + NW, bmaster(1), 1, nullptr, y2, OUT_BF16);
+        if (e == cudaSuccess && !du) e = conv(y2, wb + 2 * NW, bmaster(2), 0, nullptr, o4, OUT_F32);
+        if (e == cudaSuccess && du) e = conv(y2, wb + 2 * NW, bmaster(2), 0, nullptr, du, OUT_DU, DuArgs{out_mask, scale, clip});
         return e;
     }
     // loss and gradients into `grad` (FP32, parameter layout), loss into `loss`
@@ -791,7 +813,6 @@ struct lbm_corrector {
         }
         e = cudaGetLastError();
         const int wg = (int)std::min<int64_t>(std::max<int64_t>(n_slabs, 1), WG_CTAS);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM);
         // weight gradient of one layer: per-CTA partials, then their sum in a fixed order
         auto wgrad = [&](const __nv_bfloat16* g, const __nv_bfloat16* xin, float* out) {
             if (!n_slabs) return cudaSuccess;
@@ -800,9 +821,9 @@ struct lbm_corrector {
             return cudaGetLastError();
         };
         if (e == cudaSuccess) e = wgrad(dO, y2, grad + 2 * (NW + CH));
-        if (e == cudaSuccess) e = conv(dO, wt + 2 * NW, nullptr, 0, y2, dy2, false);  // dz2 = W3^T dO, gated by y2 > 0
+        if (e == cudaSuccess) e = conv(dO, wt + 2 * NW, nullptr, 0, y2, dy2, OUT_BF16);  // dz2 = W3^T dO, gated by y2 > 0
         if (e == cudaSuccess) e = wgrad(dy2, y1, grad + (NW + CH));
-        if (e == cudaSuccess) e = conv(dy2, wt + NW, nullptr, 0, y1, dy, false);  // dz1 = W2^T dz2, gated by y1 > 0
+        if (e == cudaSuccess) e = conv(dy2, wt + NW, nullptr, 0, y1, dy, OUT_BF16);  // dz1 = W2^T dz2, gated by y1 > 0
         if (e == cudaSuccess) e = wgrad(dy, x0, grad);
         return e;
     }
@@ -920,6 +941,16 @@ lbm_status lbm_corrector_create(const uint8_t* mask, int32_t nx, int32_t ny, int
         e = cudaMemcpyAsync(K->slabs, sv.data(), sizeof(int4) * sv.size(), cudaMemcpyHostToDevice, K->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(K->err, 0, sizeof(unsigned int), K->stream);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&K->ev, cudaEventDisableTiming);
+    {  // the convolutions' grid and their shared-memory sizes, once
+        int dev = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&K->sms, cudaDevAttrMultiProcessorCount, dev);
+        const auto smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<OUT_BF16>, smem_attr, (int)CONV_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<OUT_F32>, smem_attr, (int)CONV_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<OUT_DU>, smem_attr, (int)CONV_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad_tc, smem_attr, (int)WG_SMEM);
+    }
     {
         const __nv_bfloat16* ins[5] = {K->x0, K->y1, K->y2, K->dO, K->dy2};
         for (int t = 0; t < 5 && e == cudaSuccess; ++t) {
@@ -972,14 +1003,10 @@ lbm_status lbm_corrector_forward(lbm_corrector* K, const uint8_t* mask, const ui
 {
     NvtxRange nvtx_range("lbm_corrector_forward");
     if (!K || !rho || !u || !du) return nn_fail(LBM_ERR_INVALID_ARG, "NULL argument");
-    cudaError_t e = K->forward(mask, rho, u);
     const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
     // the slabs write their cells; the rest of the caller's box is zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(du, 0, sizeof(float) * 3 * K->n_cells, K->stream);
-    if (e == cudaSuccess && K->n_slabs) {
-        k_output<<<(unsigned)K->n_slabs, 128, 0, K->stream>>>(K->o4, om, K->box, K->du_scale, K->clip, du, K->slabs);
-        e = cudaGetLastError();
-    }
+    cudaError_t e = cudaMemsetAsync(du, 0, sizeof(float) * 3 * K->n_cells, K->stream);
+    if (e == cudaSuccess) e = K->forward(mask, rho, u, du, om, K->du_scale);
     if (e != cudaSuccess) return nn_fail(LBM_ERR_CUDA, std::string("corrector forward: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -1045,21 +1072,18 @@ lbm_status lbm_corrector_apply(lbm_corrector* K, lbm_domain* dom, const uint8_t*
     DomainAccess da{};
     if (!domain_access(dom, &da)) return nn_fail(LBM_ERR_INVALID_ARG, "NULL domain");
     // rho, u are exported on the domain's stream and the correction is applied there: the
-    // corrector's own stream waits for the one and the domain's stream for the other
-    lbm_status s = lbm_get_macroscopic(dom, K->rho, K->u, 1, 1);
-    if (s) return s;
-    cudaError_t e = cudaSuccess;
-    if (da.stream != K->stream) {
+    // corrector's own stream waits for the one and the domain's stream for the other.  The cells
+    // that are not fluid are cleared only when the staging last held another domain's export
+    // (the box is cleared once per domain, not on every call)
+    cudaError_t e = enqueue_macroscopic_dense(dom, K->rho, K->u, da.serial != K->export_serial);
+    K->export_serial = e == cudaSuccess ? da.serial : 0;
+    if (e == cudaSuccess && da.stream != K->stream) {
         e = cudaEventRecord(K->ev, da.stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(K->stream, K->ev, 0);
     }
-    if (e == cudaSuccess) e = K->forward(mask, K->rho, K->u);
     const uint8_t* om = out_mask ? out_mask : (mask ? mask : K->mask);
-    if (e == cudaSuccess && K->n_slabs) {  // cells outside the slabs keep the zero of set-up
-        k_output<<<(unsigned)K->n_slabs, 128, 0, K->stream>>>(K->o4, om, K->box, (float)(K->du_scale * gain), K->clip,
-                                                              K->du, K->slabs);
-        e = cudaGetLastError();
-    }
+    // cells outside the slabs keep the zero of set-up
+    if (e == cudaSuccess) e = K->forward(mask, K->rho, K->u, K->du, om, (float)(K->du_scale * gain));
     if (e == cudaSuccess && da.stream != K->stream) {
         e = cudaEventRecord(K->ev, K->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(da.stream, K->ev, 0);
