@@ -204,8 +204,9 @@ lbm_status lbm_get_diagnostics(lbm_domain* dom, lbm_diagnostics* out);
  * 320 KiB inside this library, present on every device that loads the library until the
  * process exits.  The paper has no counterpart; this is a library service.
  *   Limit: domains of at most 2,097,152 fluid cells (INVALID_ARG beyond, nothing launched).
- *   The first call on a device looks up the array's device address with that device current;
- *   make that first call before any stream capture.
+ *   The first call on a device looks up the array's device address with that device current.
+ *   The call waits for the domain's stream and copies the result to the host, so it must not
+ *   be made while that stream is being captured.
  *   All calls share the array; calls whose work overlaps on the GPU (domains on different
  *   streams or host threads) race on it, so serialise them.  Nothing in it needs clearing
  *   between calls: each call overwrites every word it reads.
