@@ -11,7 +11,9 @@ batched launch per step (graph chunks of 10; launch config name as the last argu
 "persistent"); corrector<edge>: the
 learned corrector's forward pass (features, three convolutions, output) on the seed-200
 synthetic aneurysm at that edge after 100 solver steps, repeated `steps` times (initial
-parameters of seed 0), with its CUDA-event time per pass.
+parameters of seed 0), with its CUDA-event time per pass; corrector_train<edge>: the same case,
+one training step per pass (forward, loss, backward with the weight gradients, Adam) toward a
+seeded perturbation of u.
 """
 import sys
 
@@ -31,22 +33,32 @@ def main(argv=None):
     if case.startswith("corrector"):
         import torch
 
-        edge = int(case[len("corrector"):] or 128)
+        train = case.startswith("corrector_train")
+        edge = int(case[len("corrector_train" if train else "corrector"):] or 128)
         g = I.aneurysm(200, edge=edge, period=2000.0 * edge / 128.0)
         net = lbm.Corrector(g.mask, I.corrector_init_params(0), 0.05, 0.01, 0.005)
         dom = lbm.Domain.from_geometry(g)
         dom.step(100)
         rho, u = dom.macroscopic_tensors()
+        u_target = u + 0.001 * torch.randn(u.shape, device=u.device, generator=torch.Generator(u.device).manual_seed(0))
+
+        def one():
+            if train:
+                net.train_step(rho, u, u_target, 1e-4)
+            else:
+                net.forward(rho, u)
+
         for _ in range(3):
-            net.forward(rho, u)
+            one()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
         for _ in range(steps):
-            net.forward(rho, u)
+            one()
         e1.record()
         torch.cuda.synchronize()
-        print(f"ok {case} fluid={g.nfluid} forward_ms={e0.elapsed_time(e1) / max(steps, 1):.4f}")
+        what = "train_step_ms" if train else "forward_ms"
+        print(f"ok {case} fluid={g.nfluid} {what}={e0.elapsed_time(e1) / max(steps, 1):.4f}")
         return
     if case == "batch16":
         import numpy as np
