@@ -438,23 +438,40 @@ __device__ __forceinline__ uint32_t wall_rules(const DomainView& v, const void* 
     uint32_t half = 0u;
     if (kind == KIND_BOUZIDI) {
         const uint32_t off = (uint32_t)(aux >= 0 ? aux : v.aux[slot]);
+        // A direction's rule reads d_i and, only when opp(i) has no link, d_opp(i), which no other
+        // direction's rule changes: the order of the directions does not matter.  The twist takes
+        // the links of nine directions at a time (their q and f*_a requested before the first is
+        // used: one memory latency per group, not per link; -26% per step on a 128^3 aneurysm);
+        // A-B, whose f*_a come from the other array, keeps one direction at a time (the grouped
+        // form spills in its 64- to 80-register configurations and was 2% slower on the pipe).
+        constexpr int GS = SCHEME == LBM_SCHEME_ESOTERIC ? 9 : 1;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (!(wm & (1u << i))) continue;
-            const uint32_t li = link_index(off, wm, i);
-            if (!LBM_IN_RANGE(li, v.n_bq, 5)) continue;
-            const float q = __ldg(v.bq + li);
-            // loaded whatever q is, so that the two loads do not wait on each other
-            const float fa = (SCHEME == LBM_SCHEME_ESOTERIC)
-                                 ? Store<ST>::load_rw(v.side, i, li)
-                                 : Store<ST>::load(src_ab, i, (uint32_t)i * (uint32_t)v.n_slots + slot);
-            if (q > 0.0f) {
-                if (q < 0.5f) {
-                    if (!(wm & (1u << (Q - 1 - i)))) d[i] = 2.0f * q * d[i] + (1.0f - 2.0f * q) * d[Q - 1 - i];
-                } else {
-                    const float inv2q = 0.5f / q;
-                    d[i] = inv2q * d[i] + (1.0f - inv2q) * fa;
-                    half |= 1u << i;
+        for (int g = 0; g < Q / GS; ++g) {
+            float qg[GS], fg[GS];
+#pragma unroll
+            for (int j = 0; j < GS; ++j) {
+                const int i = GS * g + j;
+                const uint32_t li = link_index(off, wm, i);
+                const bool has = ((wm >> i) & 1u) && LBM_IN_RANGE(li, v.n_bq, 5);
+                qg[j] = has ? __ldg(v.bq + li) : 0.0f;
+                // loaded whatever q is, so that the two loads do not wait on each other
+                fg[j] = !has ? 0.0f
+                             : (SCHEME == LBM_SCHEME_ESOTERIC)
+                                   ? Store<ST>::load_rw(v.side, i, li)
+                                   : Store<ST>::load(src_ab, i, (uint32_t)i * (uint32_t)v.n_slots + slot);
+            }
+#pragma unroll
+            for (int j = 0; j < GS; ++j) {
+                const int i = GS * g + j;
+                const float q = qg[j], fa = fg[j];
+                if (q > 0.0f) {  // 0: no link (or halfway bounce-back on this link)
+                    if (q < 0.5f) {
+                        if (!(wm & (1u << (Q - 1 - i)))) d[i] = 2.0f * q * d[i] + (1.0f - 2.0f * q) * d[Q - 1 - i];
+                    } else {
+                        const float inv2q = 0.5f / q;
+                        d[i] = inv2q * d[i] + (1.0f - inv2q) * fa;
+                        half |= 1u << i;
+                    }
                 }
             }
         }
