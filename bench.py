@@ -54,21 +54,24 @@ NOMINAL_HBM_GBS = 8000.0  # the metric's roofline denominator (bytes per fluid-c
 # configuration); reported only for the configuration the bench runs, None for any other.  An
 # entry is removed whenever the kernel it was taken on changes.
 K_STEP_TRAFFIC = {
-    ("womersley", "fp32", "ab", "128x10"): (125_316_096, "k_step<fp32, A-B, 2 bricks, 10 CTAs/SM, default rates> (87.88 MB read, 37.44 MB written)"),
-    ("womersley", "fp32", "ab", "128x6"): (120_888_320, "k_step<fp32, A-B, 2 bricks, 6 CTAs/SM, default rates> (86.96 MB read, 33.93 MB written)"),
-    ("womersley", "fp32", "ab", "128x7"): (120_780_544, "k_step<fp32, A-B, 2 bricks, 7 CTAs/SM, default rates> (87.01 MB read, 33.77 MB written)"),
-    ("womersley", "fp32", "ab", "128x8"): (120_323_072, "k_step<fp32, A-B, 2 bricks, 8 CTAs/SM, default rates> (86.95 MB read, 33.37 MB written)"),
-    ("womersley", "fp32", "ab", "256x3"): (121_214_464, "k_step<fp32, A-B, 4 bricks, 3 CTAs/SM, default rates> (86.96 MB read, 34.25 MB written)"),
-    ("womersley", "fp32", "esoteric", "128x10"): (114_500_608, "k_step<fp32, twist, 2 bricks, 10 CTAs/SM, default rates, parity 1> (83.86 MB read, 30.65 MB written)"),
-    ("womersley", "fp32", "esoteric", "128x6"): (101_432_832, "k_step<fp32, twist, 2 bricks, 6 CTAs/SM, default rates, parity 1> (82.83 MB read, 18.60 MB written)"),
-    ("womersley", "fp32", "esoteric", "128x7"): (101_049_344, "k_step<fp32, twist, 2 bricks, 7 CTAs/SM, default rates, parity 1> (82.83 MB read, 18.22 MB written)"),
-    ("womersley", "fp32", "esoteric", "128x8"): (104_847_616, "k_step<fp32, twist, 2 bricks, 8 CTAs/SM, default rates, parity 1> (83.04 MB read, 21.81 MB written)"),
-    ("womersley", "fp32", "esoteric", "256x3"): (101_245_440, "k_step<fp32, twist, 4 bricks, 3 CTAs/SM, default rates, parity 1> (82.82 MB read, 18.43 MB written)"),
-    ("womersley", "fp32", "esoteric", "2c128x3"): (101_358_592, "k_step2<fp32, 4 bricks, 3 CTAs/SM> (82.85 MB read, 18.51 MB written)"),
-    ("womersley", "fp32", "esoteric", "2c128x4"): (101_316_096, "k_step2<fp32, 4 bricks, 4 CTAs/SM> (82.85 MB read, 18.46 MB written)"),
-    ("aneurysm512", "fp32", "esoteric", "128x8"): (257_089_536,
+    ("womersley", "fp32", "ab", "128x10"): (125_738_240, "k_step<fp32, A-B, 2 bricks, 10 CTAs/SM, default rates> (88.68 MB read, 37.06 MB written)"),
+    ("womersley", "fp32", "ab", "128x6"): (121_100_544, "k_step<fp32, A-B, 2 bricks, 6 CTAs/SM, default rates> (86.99 MB read, 34.11 MB written)"),
+    ("womersley", "fp32", "ab", "128x7"): (120_878_592, "k_step<fp32, A-B, 2 bricks, 7 CTAs/SM, default rates> (87.03 MB read, 33.85 MB written)"),
+    ("womersley", "fp32", "ab", "128x8"): (120_099_840, "k_step<fp32, A-B, 2 bricks, 8 CTAs/SM, default rates> (86.96 MB read, 33.14 MB written)"),
+    ("womersley", "fp32", "ab", "256x3"): (121_325_824, "k_step<fp32, A-B, 4 bricks, 3 CTAs/SM, default rates> (86.97 MB read, 34.35 MB written)"),
+    ("womersley", "fp32", "esoteric", "128x10"): (116_750_592, "k_step<fp32, twist, 2 bricks, 10 CTAs/SM, default rates, parity 1> (84.08 MB read, 32.68 MB written)"),
+    ("womersley", "fp32", "esoteric", "128x6"): (101_404_160, "k_step<fp32, twist, 2 bricks, 6 CTAs/SM, default rates, parity 1> (82.83 MB read, 18.57 MB written)"),
+    ("womersley", "fp32", "esoteric", "128x7"): (101_440_256, "k_step<fp32, twist, 2 bricks, 7 CTAs/SM, default rates, parity 1> (82.83 MB read, 18.61 MB written)"),
+    ("womersley", "fp32", "esoteric", "128x8"): (106_862_336, "k_step<fp32, twist, 2 bricks, 8 CTAs/SM, default rates, parity 1> (83.17 MB read, 23.69 MB written)"),
+    ("womersley", "fp32", "esoteric", "256x3"): (100_946_944, "k_step<fp32, twist, 4 bricks, 3 CTAs/SM, default rates, parity 1> (82.82 MB read, 18.13 MB written)"),
+    ("womersley", "fp32", "esoteric", "2c128x3"): (101_332_224, "k_step2<fp32, 4 bricks, 3 CTAs/SM> (82.85 MB read, 18.48 MB written)"),
+    ("womersley", "fp32", "esoteric", "2c128x4"): (102_119_680, "k_step2<fp32, 4 bricks, 4 CTAs/SM> (82.90 MB read, 19.22 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "128x7"): (250_688_512,
+                                                   "k_step<fp32, twist, 2 bricks, 7 CTAs/SM, default rates, parity 1> "
+                                                   "(165.51 MB read, 85.18 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "128x8"): (260_912_896,
                                                    "k_step<fp32, twist, 2 bricks, 8 CTAs/SM, default rates, parity 1> "
-                                                   "(165.96 MB read, 91.13 MB written)"),
+                                                   "(166.24 MB read, 94.67 MB written)"),
 }
 
 
