@@ -66,6 +66,13 @@ K_STEP_TRAFFIC = {
     ("womersley", "fp32", "esoteric", "256x3"): (100_946_944, "k_step<fp32, twist, 4 bricks, 3 CTAs/SM, default rates, parity 1> (82.82 MB read, 18.13 MB written)"),
     ("womersley", "fp32", "esoteric", "2c128x3"): (101_332_224, "k_step2<fp32, 4 bricks, 3 CTAs/SM> (82.85 MB read, 18.48 MB written)"),
     ("womersley", "fp32", "esoteric", "2c128x4"): (102_119_680, "k_step2<fp32, 4 bricks, 4 CTAs/SM> (82.90 MB read, 19.22 MB written)"),
+    ("womersley", "fp32", "esoteric", "pipe128x6"): (98_264_576, "k_step_et_pipe<fp32, 2 bricks, 6 CTAs/SM, persistent> (79.99 MB read, 18.27 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "256x3"): (250_623_744, "k_step<fp32, twist, 4 bricks, 3 CTAs/SM, default rates, parity 1> (165.48 MB read, 85.14 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "128x6"): (250_743_296, "k_step<fp32, twist, 2 bricks, 6 CTAs/SM, default rates, parity 1> (165.51 MB read, 85.24 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "128x10"): (285_614_080, "k_step<fp32, twist, 2 bricks, 10 CTAs/SM, default rates, parity 1> (171.06 MB read, 114.56 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "2c128x4"): (251_746_304, "k_step2<fp32, 4 bricks, 4 CTAs/SM> (165.76 MB read, 85.98 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "2c128x3"): (250_264_320, "k_step2<fp32, 4 bricks, 3 CTAs/SM> (165.71 MB read, 84.56 MB written)"),
+    ("aneurysm512", "fp32", "esoteric", "pipe128x6"): (245_090_048, "k_step_et_pipe<fp32, 2 bricks, 6 CTAs/SM, persistent> (159.69 MB read, 85.40 MB written)"),
     ("aneurysm512", "fp32", "esoteric", "128x7"): (250_688_512,
                                                    "k_step<fp32, twist, 2 bricks, 7 CTAs/SM, default rates, parity 1> "
                                                    "(165.51 MB read, 85.18 MB written)"),
